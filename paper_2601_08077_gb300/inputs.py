@@ -1,0 +1,235 @@
+"""Seeded synthetic inputs for the density-fitting J/K hot path.
+
+This module is the input generator shared by the CUDA path, the tests and the
+benchmark.  It draws geometries, basis exponents and orbitals, and it
+synthesises the DF tensor B of Eq. cderi (Section 2.1) from closed-form
+s-type Gaussian integrals.  It holds none of the hot-path arithmetic (no
+split, no slice products, no rho/J/K): those live in the CUDA library and,
+independently, in the CPU oracle.
+
+Recipe (the paper's molecules and basis sets are not available, so these
+stand in for Table 3's systems, which have N_aux/N_bf = 1.9-4.6 and
+N_occ/N_bf = 0.07-0.16):
+
+* geometry: ``n`` atoms drawn one by one, uniform in a cube of edge
+  ``L = 10 (n/20)^{1/3}`` bohr (constant atom density), rejecting any draw
+  closer than 1.5 bohr to an accepted atom; numpy PCG64 ``default_rng(seed)``;
+* basis: per atom 5 AO exponents geometric in [0.1, 10] and 15 auxiliary
+  exponents geometric in [0.05, 20], atom-major, normalised primitives;
+* B = L^{-1} (P|mu nu) with L L^T = (P|Q) (Eq. cderi), via LAPACK's Cholesky
+  and triangular solve;
+* orbitals: C = Q factor of the reduced QR of a seeded N(0,1) nao x nocc
+  matrix, D = 2 C C^T;
+* SCF-like sequence: orbitals perturbed off span(C*) so that
+  ||D_k - D*||_F = 0.1 * 10^-k.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_GEN_SRC = os.path.join(_HERE, "csrc", "gen_integrals.c")
+_GEN_LIB = os.path.join(_HERE, "_build", "libdfgen.so")
+
+AO_EXPONENTS = np.geomspace(0.1, 10.0, 5)
+AUX_EXPONENTS = np.geomspace(0.05, 20.0, 15)
+MIN_SEPARATION = 1.5
+AUX_BLOCK = 128  # auxiliary functions per block (Eqs. df-k-blk-1/2)
+
+
+def build_generator_library(force: bool = False) -> str:
+    """Compile the C integral generator (host code) into ``_build/``."""
+    if force or not os.path.exists(_GEN_LIB) or (
+            os.path.getmtime(_GEN_LIB) < os.path.getmtime(_GEN_SRC)):
+        os.makedirs(os.path.dirname(_GEN_LIB), exist_ok=True)
+        tmp = _GEN_LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", _GEN_SRC,
+                               "-o", tmp, "-lm"])
+        os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+_lib = None
+
+
+def _genlib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build_generator_library())
+        dp = ctypes.POINTER(ctypes.c_double)
+        _lib.gen_int3c.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp]
+        _lib.gen_metric.argtypes = [ctypes.c_int, dp, dp, dp]
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@dataclass
+class Molecule:
+    n_atoms: int
+    seed: int
+    edge: float
+    xyz: np.ndarray                      # [n_atoms, 3] bohr
+    ao_xyz: np.ndarray = field(repr=False)
+    ao_exp: np.ndarray = field(repr=False)
+    aux_xyz: np.ndarray = field(repr=False)
+    aux_exp: np.ndarray = field(repr=False)
+
+    @property
+    def nao(self) -> int:
+        return len(self.ao_exp)
+
+    @property
+    def naux(self) -> int:
+        return len(self.aux_exp)
+
+
+def default_edge(n_atoms: int) -> float:
+    return 10.0 * (n_atoms / 20.0) ** (1.0 / 3.0)
+
+
+def geometry(n_atoms: int, seed: int, edge: float) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    pts = np.empty((0, 3))
+    tries = 0
+    while len(pts) < n_atoms:
+        p = rng.uniform(0.0, edge, 3)
+        tries += 1
+        if tries > 1000 * n_atoms + 10000:
+            raise RuntimeError("geometry: cannot place %d atoms in a %.2f bohr cube" % (n_atoms, edge))
+        if len(pts) == 0 or np.min(np.sqrt(((pts - p) ** 2).sum(1))) >= MIN_SEPARATION:
+            pts = np.vstack([pts, p])
+    return pts
+
+
+def molecule(n_atoms: int, seed: int, edge: float | None = None) -> Molecule:
+    edge = default_edge(n_atoms) if edge is None else float(edge)
+    xyz = geometry(n_atoms, seed, edge)
+    return Molecule(
+        n_atoms=n_atoms, seed=seed, edge=edge, xyz=xyz,
+        ao_xyz=np.ascontiguousarray(np.repeat(xyz, len(AO_EXPONENTS), axis=0)),
+        ao_exp=np.tile(AO_EXPONENTS, n_atoms),
+        aux_xyz=np.ascontiguousarray(np.repeat(xyz, len(AUX_EXPONENTS), axis=0)),
+        aux_exp=np.tile(AUX_EXPONENTS, n_atoms))
+
+
+def int3c(mol: Molecule) -> np.ndarray:
+    out = np.empty((mol.naux, mol.nao, mol.nao))
+    _genlib().gen_int3c(mol.nao, mol.naux, _ptr(mol.ao_xyz), _ptr(mol.ao_exp),
+                        _ptr(mol.aux_xyz), _ptr(mol.aux_exp), _ptr(out))
+    return out
+
+
+def metric(mol: Molecule) -> np.ndarray:
+    out = np.empty((mol.naux, mol.naux))
+    _genlib().gen_metric(mol.naux, _ptr(mol.aux_xyz), _ptr(mol.aux_exp), _ptr(out))
+    return out
+
+
+def df_tensor(mol: Molecule) -> np.ndarray:
+    """B[P, mu, nu] = sum_Q L^{-1}[P, Q] (Q|mu nu), L L^T = (P|Q) (Eq. cderi)."""
+    import scipy.linalg as sl
+    V = metric(mol)
+    L = sl.cholesky(V, lower=True, check_finite=False)
+    T = int3c(mol).reshape(mol.naux, -1)
+    B = sl.solve_triangular(L, T, lower=True, overwrite_b=True, check_finite=False)
+    return np.ascontiguousarray(B.reshape(mol.naux, mol.nao, mol.nao))
+
+
+def orbitals(nao: int, nocc: int, seed: int) -> np.ndarray:
+    """Orthonormal occupied coefficients C [nao, nocc] (QR of seeded N(0,1))."""
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((nao, nocc)))
+    return np.ascontiguousarray(q)
+
+
+def density(C: np.ndarray) -> np.ndarray:
+    return 2.0 * C @ C.T
+
+
+def perturbed_orbitals(C_star: np.ndarray, k: int, seed: int, base: float = 0.1) -> tuple[np.ndarray, float]:
+    """Orbitals C_k of the SCF-like sequence: ||2 C_k C_k^T - D*||_F ~= base*10^-k.
+
+    C_k is the Q factor of C* + t Z with Z seeded N(0,1) projected off
+    span(C*); t is rescaled by a few secant steps so that the density change
+    hits its target.  Returns (C_k, achieved norm).
+    """
+    nao, nocc = C_star.shape
+    rng = np.random.default_rng(seed)
+    Z = rng.standard_normal((nao, nocc))
+    Z -= C_star @ (C_star.T @ Z)
+    Z /= np.linalg.norm(Z)
+    D_star = density(C_star)
+    target = base * 10.0 ** (-k)
+
+    def dnorm(t):
+        q, _ = np.linalg.qr(C_star + t * Z)
+        return q, np.linalg.norm(density(q) - D_star)
+
+    t = target / (2.0 * np.sqrt(2.0))   # ||dD|| ~ 2 sqrt(2) t for small t
+    q, got = dnorm(t)
+    for _ in range(3):
+        if got <= 0 or not np.isfinite(got):
+            break
+        t *= target / got
+        q, got = dnorm(t)
+    return np.ascontiguousarray(q), float(got)
+
+
+def aux_blocks(naux: int, block: int = AUX_BLOCK) -> list[tuple[int, int]]:
+    return [(p0, min(p0 + block, naux)) for p0 in range(0, naux, block)]
+
+
+# --- the workloads -----------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    n_atoms: int
+    nocc: int
+    seed: int
+
+    @property
+    def nao(self):
+        return 5 * self.n_atoms
+
+    @property
+    def naux(self):
+        return 15 * self.n_atoms
+
+
+# One molecule of 20 atoms (nao 100, naux 300, nocc 20): plain FP64 J/K.
+SMALL = Workload("df-20atom-nao100-naux300-nocc20", 20, 20, 1000 * 0 + 0)
+# One molecule of 120 atoms (nao 600, naux 1800, nocc 120): fixed-slice sweep.
+MEDIUM = Workload("df-120atom-nao600-naux1800-nocc120", 120, 120, 1000 * 1 + 0)
+# One molecule of 240 atoms (nao 1200, naux 3600, nocc 250): adaptive sequence.
+LARGE = Workload("df-240atom-nao1200-naux3600-nocc250", 240, 250, 1000 * 2 + 0)
+
+
+def batch_workloads(n_mol: int = 48, seed: int = 3000) -> list[Workload]:
+    """Grouped batch: atom counts uniform in [30, 120], nocc = nao/5."""
+    rng = np.random.default_rng(seed)
+    atoms = rng.integers(30, 121, size=n_mol)
+    return [Workload("batch-%02d" % i, int(a), int(a), seed + 1 + i) for i, a in enumerate(atoms)]
+
+
+def training_workloads(n_mol: int = 200, seed: int = 4000) -> list[Workload]:
+    """Predictor training set: nao 100..600 (20..120 atoms), nocc = nao/5."""
+    rng = np.random.default_rng(seed)
+    atoms = rng.integers(20, 121, size=n_mol)
+    return [Workload("train-%03d" % i, int(a), int(a), seed + 1 + i) for i, a in enumerate(atoms)]
+
+
+def make_inputs(w: Workload):
+    """(molecule, B, C, D) for a workload; orbitals use seed+1."""
+    mol = molecule(w.n_atoms, w.seed)
+    B = df_tensor(mol)
+    C = orbitals(mol.nao, w.nocc, w.seed + 1)
+    return mol, B, C, density(C)
