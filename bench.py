@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the DF J/K hot path on GB300.
+
+One step = one SCF-like iteration of the paper's method on one synthetic
+molecule: the FP64 Coulomb build (rho, J), the exchange build with both
+contractions emulated over INT8 slices, the energies, and the adaptive
+precision rule (Table 1) picking the next slice count.  The slice count in the
+timed steps is the one the rule selects at level 2 (5 slices), the first level
+whose emulation meets max|dK| <= 1e-10 max|K|; every run checks that gate
+against the native-FP64 build of the same K on the same GPU.
+
+metric: effective FP64 TFLOP/s of the exchange build, F_K = 4 nao^2 naux nocc
+(the paper's FLOP model with dense B, Section 3.1) per step, divided by the
+step time.  The inputs (B is 5.2 GB for the 120-atom molecule) are far larger
+than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N --steps K --warmup W --impl ours|reference
+                        --workload medium|small|large --nslices S]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DF K-build effective FP64 TFLOP/s, INT8-adaptive vs native FP64, max|dK|<=1e-10"
+UNIT = "TFLOP/s"
+LAUNCHES_PER_STEP = 9      # rho, coulomb, split C, GEMM1, split X, GEMM2, reduce, 2 energy kernels
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["small", "profile", "medium", "large"], default="medium")
+    ap.add_argument("--nslices", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2601_08077_gb300 import inputs
+    return {"small": inputs.SMALL, "profile": inputs.PROFILE, "medium": inputs.MEDIUM,
+            "large": inputs.LARGE}[name]
+
+
+def flops_K(w):
+    return 4.0 * w.nao ** 2 * w.naux * w.nocc
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "df_clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(B, C, w, budget_s=15.0):
+    """The oracle as it stands on the host cores, on a bounded sample: the exchange
+    build of whole 128-function auxiliary blocks, scaled to the metric's unit."""
+    from oracle import df_oracle as O
+    cores = len(os.sched_getaffinity(0))
+    nb, t_total, flops = 0, 0.0, 0.0
+    while t_total < budget_s and nb * 128 < w.naux:
+        p0, p1 = nb * 128, min(w.naux, nb * 128 + 128)
+        t0 = time.perf_counter()
+        O.exchange(B[p0:p1], C)
+        t_total += time.perf_counter() - t0
+        flops += 4.0 * w.nao ** 2 * (p1 - p0) * w.nocc
+        nb += 1
+    return {"value": flops / t_total / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle FP64 exchange build (NumPy, Eqs. df-k-1/2) of %d of %d auxiliary blocks "
+                      "(%d functions) of the %s workload, %.1f s" % (nb, (w.naux + 127) // 128,
+                                                                     min(w.naux, nb * 128), w.name, t_total)}
+
+
+def run_reference(args, w):
+    """--impl reference: the CPU oracle, timed per step on a bounded sample."""
+    from oracle import df_oracle as O
+    from paper_2601_08077_gb300 import inputs
+    mol, B, C, D = inputs.make_inputs(w)
+    cores = len(os.sched_getaffinity(0))
+    nblk = max(1, min((w.naux + 127) // 128, 2))
+
+    def step():
+        p1 = min(w.naux, nblk * 128)
+        O.exchange(B[:p1], C)
+        return 4.0 * w.nao ** 2 * p1 * w.nocc
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    fl = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = fl / dt / 1e12
+    sample = "oracle FP64 exchange build of the first %d auxiliary blocks of %s per step" % (nblk, w.name)
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w.name, "nao": w.nao, "naux": w.naux, "nocc": w.nocc, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = workload(args.workload)
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, w)), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2601_08077_gb300 import build, df, inputs
+    if rank == 0 or world == 1:
+        build.build_all()
+    if world > 1:
+        dist.barrier()
+
+    mol, B, C, D = inputs.make_inputs(w)
+    dev = torch.device("cuda", local)
+    Bg = torch.from_numpy(B).to(dev)
+    Cg = torch.from_numpy(C).to(dev)
+    Dg = torch.from_numpy(D).to(dev)
+    ctx = df.Context(w.nao, w.naux, w.nocc)
+    ctx.setup(Bg)
+    J = torch.empty((w.nao, w.nao), dtype=torch.float64, device=dev)
+    K = torch.empty_like(J)
+    rho = torch.empty(w.naux, dtype=torch.float64, device=dev)
+    s = args.nslices
+
+    # accuracy gate against the native FP64 build on the same GPU
+    K64 = ctx.build_K(Cg, 0)[0].clone()
+    Ks = ctx.build_K(Cg, s)[0]
+    scale = float(K64.abs().max())
+    dK = float((Ks - K64).abs().max()) / scale
+    ctx.build_J(Dg, J, rho)
+    E_fp64 = ctx.energy(Dg, J, K64, rho)
+    E_s = ctx.energy(Dg, J, Ks, rho)
+    dE = abs((E_s[0] + E_s[2]) - (E_fp64[0] + E_fp64[2]))
+    ctx.sync_status()
+
+    ctx.adaptive_reset()
+
+    def step():
+        ctx.build_J(Dg, J, rho)
+        ctx.build_K(Cg, s, K)
+        e = ctx.energy(Dg, J, K, rho)
+        ctx.adaptive_next(e[0] + e[2])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.phase_times()
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ctx.set_profiling(False)
+    phases = ctx.phase_times()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ctx.sync_status()
+
+    # native FP64 exchange build, same GPU, same B (the comparison build)
+    nfp = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(nfp):
+        ctx.build_K(Cg, 0, K)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_fp64 = f0.elapsed_time(f1) / nfp
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    Ch = torch.from_numpy(C).pin_memory()
+    Dh = torch.from_numpy(D).pin_memory()
+    Jh = torch.empty((w.nao, w.nao), dtype=torch.float64).pin_memory()
+    Kh = torch.empty_like(Jh).pin_memory()
+    Cd = torch.empty_like(Cg)
+    Dd = torch.empty_like(Dg)
+
+    def step_e2e():
+        Cd.copy_(Ch, non_blocking=True)
+        Dd.copy_(Dh, non_blocking=True)
+        ctx.build_J(Dd, J, rho)
+        ctx.build_K(Cd, s, K)
+        e = ctx.energy(Dd, J, K, rho)
+        Jh.copy_(J, non_blocking=True)
+        Kh.copy_(K, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        ctx.adaptive_next(e[0] + e[2])
+
+    step_e2e()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    ms_e2e = (time.perf_counter() - t0) / args.steps * 1e3
+    h2d = C.nbytes + D.nbytes
+    d2h = 2 * w.nao * w.nao * 8 + 3 * 8
+
+    FK = flops_K(w)
+    value = FK * world / (ms * 1e-3) / 1e12
+    # roofline of the dominant kernel (the slice GEMM launch with the largest share)
+    pk, src = peaks()
+    g1_ms = phases["gemm1"][0] / max(1, phases["gemm1"][1])
+    g2_ms = phases["gemm2"][0] / max(1, phases["gemm2"][1])
+    pairs = s * (s + 1) // 2
+    g1_flops = pairs * 2.0 * w.nocc * w.naux * w.nao * w.nao
+    g2_flops = pairs * 2.0 * (w.nao * (w.nao + 1) / 2) * w.naux * w.nocc
+    if g1_ms >= g2_ms:
+        kname, kms, kfl = "slice_gemm (X = B C)", g1_ms, g1_flops
+    else:
+        kname, kms, kfl = "slice_gemm (K_b = X_b X_b^T)", g2_ms, g2_flops
+    peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
+    achieved = kfl / (kms * 1e-3) / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (INT8 slices as BF16 on tcgen05, exact INT accumulation)",
+        "data": "synthetic (seeded s-type Gaussian molecule, integrals and DF tensor generated)",
+        "config": {"workload": w.name, "nao": w.nao, "naux": w.naux, "nocc": w.nocc, "nslices": s,
+                   "level": 2, "l2": "inputs larger than L2 (B %.1f GB)" % (B.nbytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": FK / (ms_e2e * 1e-3) / 1e12 * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "roofline": {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "bf16_tflops_sustained (%s)" % src,
+                     "algorithmic": "s(s+1)/2 slice-pair products x 2 flops per multiply-add, no padding"},
+        "accuracy": {"max_dK_rel_vs_fp64": dK, "dE_vs_fp64": dE, "gate_1e-10": dK <= 1e-10},
+        "fp64_native": {"k_build_ms": ms_fp64, "tflops": FK / (ms_fp64 * 1e-3) / 1e12,
+                        "speedup_of_int8": ms_fp64 / (phases_k_ms(phases, args.steps))},
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "k_build_tflops": FK / (phases_k_ms(phases, args.steps) * 1e-3) / 1e12,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(B, C, w)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def phases_k_ms(phases, steps):
+    return sum(phases[k][0] for k in ("split_C", "gemm1", "split_X", "gemm2", "reduce")) / steps
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * libdf: GB300-native adaptive-precision density fitting (C ABI).
+ *
+ * The hot path of arXiv 2601.08077 ("Accelerating Density Fitting with
+ * Adaptive-precision and 8-bit Integer on AI Accelerators"):
+ *
+ *   Coulomb  (Section 2.1, Eqs. df-j-1, df-j-2):  rho_P = sum_mn B_Pmn D_mn,
+ *                                                 J_mn  = sum_P B_Pmn rho_P      (FP64)
+ *   Exchange (Section 2.1, Eqs. df-k-1, df-k-2):  X_Pmi = sum_n B_Pmn C_ni,
+ *                                                 K_mn  = sum_Pi X_Pmi X_Pni
+ *   with both exchange contractions run as FP64-emulating GEMMs over s INT8
+ *   slices (Section 3.2), blocked over 128 auxiliary functions
+ *   (Section 3.3, Eqs. df-k-blk-1/2), and s chosen by the energy-change rule
+ *   of Table 1 (Section 3.2) or per block by a learned predictor.
+ *
+ * Conventions (every entry point):
+ *   - Matrices are row-major FP64.  B is [naux][nao][nao], C is [nao][nocc],
+ *     D, J and K are [nao][nao], rho is [naux].
+ *   - Pointers named *_dev are device pointers owned by the caller; the
+ *     library never frees them.  The context owns its own workspaces
+ *     (digit planes, exponents, X, partial K blocks), allocated by df_create.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  All calls are asynchronous on that stream unless
+ *     stated otherwise.
+ *   - Errors: every call returns a df_status.  A context keeps the first
+ *     error it saw (df_last_error).  Device-side waits are bounded; a wait
+ *     that runs out sets DF_ERR_TIMEOUT in the context's device status word,
+ *     which df_sync_status reads.  No call traps or aborts the process.
+ */
+#ifndef DF_H_
+#define DF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DF_OK = 0,
+  DF_ERR_ARG = -1,      /* invalid argument (size, pointer, slice count) */
+  DF_ERR_CUDA = -2,     /* a CUDA runtime / cuBLAS call failed */
+  DF_ERR_OOM = -3,      /* device allocation failed */
+  DF_ERR_NOT_PD = -4,   /* metric not positive definite */
+  DF_ERR_TIMEOUT = -5,  /* a bounded device-side wait ran out */
+  DF_ERR_TOL = -6,      /* a result missed its tolerance after recompute */
+  DF_ERR_STATE = -7     /* call out of order (e.g. build before setup) */
+} df_status;
+
+typedef struct df_ctx df_ctx;
+
+#define DF_S_MAX 8        /* digits per value: 8 x 8 bits >= the 63 bits of RNE(x 2^63) */
+#define DF_AUX_BLOCK 128  /* auxiliary functions per block (Section 3.3) */
+
+/* Statistics of one exchange build (host struct, optional). */
+typedef struct {
+  int nblk;                 /* number of auxiliary blocks */
+  int slices[256];          /* slice count used per block (first 256 blocks) */
+  int recomputed;           /* blocks recomputed at more slices */
+  int fallback;             /* 1 if the build ran in native FP64 */
+} df_kstats;
+
+/* Create a context for one molecule: nao basis functions, naux auxiliary
+ * functions, up to nocc_max occupied orbitals, digit planes kept for B up to
+ * s_max (1..8).  Allocates all device workspaces on the current device.
+ * Returns DF_ERR_OOM if they do not fit. */
+df_status df_create(df_ctx **out, int nao, int naux, int nocc_max, int s_max);
+void df_destroy(df_ctx *ctx);
+
+/* Attach the DF tensor B (Eq. cderi; device, [naux][nao][nao], caller-owned
+ * and kept alive for the context's lifetime) and split it once into s_max
+ * INT8 digit planes with one power-of-two exponent per (P, mu) row
+ * (Section 3.2).  B is constant over the SCF iterations, so this runs once. */
+df_status df_setup(df_ctx *ctx, const double *B_dev, void *stream);
+
+/* Coulomb build in FP64 (Eqs. df-j-1, df-j-2; the paper keeps J in FP64,
+ * Section 3.1).  D_dev symmetric [nao][nao]; J_dev [nao][nao] out;
+ * rho_dev [naux] out (may be NULL: then an internal buffer is used). */
+df_status df_build_J(df_ctx *ctx, const double *D_dev, double *J_dev, double *rho_dev, void *stream);
+
+/* Exchange build (Eqs. df-k-1, df-k-2, blocked as Eqs. df-k-blk-1/2).
+ * C_dev [nao][nocc] (nocc <= nocc_max), K_dev [nao][nao] out (full,
+ * symmetric).  nslices: 1..8 = INT8 emulation with that many slices per
+ * operand for every block; 0 = native FP64 (cuBLAS DGEMM + DSYRK, the
+ * comparison build).  stats may be NULL. */
+df_status df_build_K(df_ctx *ctx, const double *C_dev, int nocc, int nslices, double *K_dev,
+                     df_kstats *stats, void *stream);
+
+/* Exchange build with one slice count per auxiliary block (host array of
+ * ceil(naux/128) entries, each 1..8).  Used by the learned predictor. */
+df_status df_build_K_blocks(df_ctx *ctx, const double *C_dev, int nocc, const int *slices_per_block,
+                            double *K_dev, df_kstats *stats, void *stream);
+
+/* Energies (the benchmark spec's E_J and E_K, FP64 reductions on the device):
+ * E_host[0] = 1/2 tr(D J), E_host[1] = 1/2 rho.rho (second route to E_J),
+ * E_host[2] = -1/2 tr(D K).  Synchronises `stream`; rho_dev may be NULL
+ * (then the buffer of the last df_build_J is used). */
+df_status df_energy(df_ctx *ctx, const double *D_dev, const double *J_dev, const double *K_dev,
+                    const double *rho_dev, double *E_host, void *stream);
+
+/* Split rows of an FP64 matrix (device [rows][ld], cols used) into nslices
+ * balanced INT8 digits (Section 3.2): exps_dev [rows] (int32) gets the
+ * smallest e with max|row| < 127/128 2^e, digits_dev [nslices][rows][cols]
+ * (int8) gets d_0..d_{nslices-1} of RNE(A 2^{63-e}).  No context needed. */
+df_status df_split_int8(const double *A_dev, int rows, int cols, int ld, int nslices, int32_t *exps_dev,
+                        int8_t *digits_dev, void *stream);
+
+/* Exact INT32-range slice-pair products S_g = sum_{t+u=g} A_t B_u^T for
+ * g < nslices (Section 3.2) of A (device [M][K]) and B (device [N][K]), both
+ * split per row on the device, computed on the tensor cores.  S_dev
+ * [nslices][N][M] int64 (note: N-major).  Exps: ea_dev [M], eb_dev [N]
+ * (may be NULL).  Test and inspection entry point. */
+df_status df_slice_products(const double *A_dev, const double *B_dev, int M, int N, int K, int nslices,
+                            int64_t *S_dev, int32_t *ea_dev, int32_t *eb_dev, void *stream);
+
+/* FP64-emulated product out = A B^T (A [M][K], B [N][K], out [M][N], all
+ * device, row-major) with nslices INT8 slices per operand (Section 3.2). */
+df_status df_emulated_gemm(const double *A_dev, const double *B_dev, int M, int N, int K, int nslices,
+                           double *out_dev, void *stream);
+
+/* Table 1 (Section 3.2): the emulation level for the next iteration given the
+ * relative energy change (>= lower bound of the row); level 0 = FP64. */
+int df_level_for(double dE_rel);
+/* INT8 splits of a level: 4->3, 3->4, 2->5, 1->6, 0->0 (FP64). */
+int df_level_slices(int level);
+
+/* Adaptive controller kept in the context (Section 3.2): call once per
+ * iteration with the energy it produced; returns the level for the next
+ * iteration.  Iterations 0 and 1 run at level 4; afterwards the level is
+ * min(previous, rule(dE_rel)) - precision never drops.  If fp64_from_level
+ * >= 0, any level <= it is run as native FP64 (the hardware-specific
+ * fallback of Section 3.2). */
+df_status df_adaptive_reset(df_ctx *ctx, int fp64_from_level);
+df_status df_adaptive_next(df_ctx *ctx, double energy, int *level_out, int *nslices_out);
+
+/* Read (and clear) the device status word; synchronises `stream`. */
+df_status df_sync_status(df_ctx *ctx, void *stream);
+df_status df_last_error(const df_ctx *ctx);
+const char *df_strerror(df_status s);
+
+/* Phases timed when profiling is on (CUDA events on the call's stream). */
+#define DF_PHASE_SPLIT_C 0  /* C -> digit planes */
+#define DF_PHASE_GEMM1 1    /* X = B C on the tensor cores (or cuBLAS DGEMM in FP64 mode) */
+#define DF_PHASE_SPLIT_X 2  /* X -> per-(block, mu) digit planes */
+#define DF_PHASE_GEMM2 3    /* K_b = X_b X_b^T on the tensor cores (or cuBLAS DSYRK) */
+#define DF_PHASE_REDUCE 4   /* K = sum_b K_b */
+#define DF_PHASE_RHO 5      /* rho = B . D */
+#define DF_PHASE_COULOMB 6  /* J = B^T rho */
+#define DF_PHASE_ENERGY 7   /* energy reductions */
+#define DF_NPHASES 8
+
+/* Turn per-phase event timing on or off (off by default; costs two event
+ * records per phase). */
+df_status df_set_profiling(df_ctx *ctx, int on);
+/* Summed phase times (ms) and record counts since the last read, for the
+ * DF_NPHASES phases; waits for the recorded events and clears them. */
+df_status df_phase_times(df_ctx *ctx, double *ms, int *count);
+
+/* Device bytes held by the context's workspaces. */
+int64_t df_workspace_bytes(const df_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DF_H_ */

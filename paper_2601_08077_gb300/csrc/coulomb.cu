@@ -1,0 +1,158 @@
+// Coulomb build in FP64 (Section 2.1, Eqs. df-j-1 and df-j-2) and the energy
+// reductions.
+//
+//   rho_P = sum_mn B_Pmn D_mn     (one streaming pass over B)
+//   J_mn  = sum_P B_Pmn rho_P     (a second streaming pass over B)
+//
+// Both B_P and D are symmetric (D by the paper's assumption in Section 2.1,
+// B_P by construction), so each pass reads only the upper triangle of every
+// B_P: nao(nao+1)/2 doubles per auxiliary function instead of nao^2.  That
+// halves the DRAM bytes and the FP64 FMAs of the paper's 4 N_scr N_aux
+// (Section 3.1).  On GB300 the FP64 pipe is narrow, so these kernels are
+// bounded by FP64 FMA throughput rather than by HBM; the roofline reported
+// for them uses the measured FP64 rate.
+#include "df_internal.h"
+
+namespace df {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One CTA per P.  Warp w takes rows mu = w, w + 8, ...; lanes stride nu >= mu.
+__global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, const double *__restrict__ D,
+                                                  int nao, double *__restrict__ rho) {
+  const int P = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double *BP = B + (long long)P * nao * nao;
+  double off = 0.0, dia = 0.0;
+  for (int mu = warp; mu < nao; mu += 8) {
+    const double *brow = BP + (long long)mu * nao;
+    const double *drow = D + (long long)mu * nao;
+    if (lane == 0) dia = fma(__ldg(brow + mu), __ldg(drow + mu), dia);
+    for (int nu = mu + 1 + lane; nu < nao; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+  }
+  double v = 2.0 * off + dia;
+  v = warp_sum(v);
+  __shared__ double red[8];
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    rho[P] = s;
+  }
+}
+
+// Thread per (mu, nu >= mu): J_mn = sum_P B_Pmn rho_P, written to both halves.
+__global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__ B, const double *__restrict__ rho,
+                                                      int naux, int nao, double *__restrict__ J) {
+  extern __shared__ double srho[];
+  for (int i = threadIdx.x; i < naux; i += blockDim.x) srho[i] = rho[i];
+  __syncthreads();
+  const int mu = blockIdx.y;
+  const int nu = mu + blockIdx.x * blockDim.x + threadIdx.x;
+  if (nu >= nao) return;
+  const long long off = (long long)mu * nao + nu;
+  const long long stride = (long long)nao * nao;
+  double acc = 0.0;
+  int P = 0;
+  for (; P + 4 <= naux; P += 4) {
+    const double b0 = __ldg(B + (P + 0) * stride + off);
+    const double b1 = __ldg(B + (P + 1) * stride + off);
+    const double b2 = __ldg(B + (P + 2) * stride + off);
+    const double b3 = __ldg(B + (P + 3) * stride + off);
+    acc = fma(b0, srho[P + 0], acc);
+    acc = fma(b1, srho[P + 1], acc);
+    acc = fma(b2, srho[P + 2], acc);
+    acc = fma(b3, srho[P + 3], acc);
+  }
+  for (; P < naux; ++P) acc = fma(__ldg(B + P * stride + off), srho[P], acc);
+  J[(long long)mu * nao + nu] = acc;
+  J[(long long)nu * nao + mu] = acc;
+}
+
+// Partial sums: [0] sum D.J, [1] sum rho.rho, [2] sum D.K, one triple per block.
+__global__ void __launch_bounds__(256) energy_partials_kernel(const double *__restrict__ D,
+                                                              const double *__restrict__ J,
+                                                              const double *__restrict__ K,
+                                                              const double *__restrict__ rho, long long n2,
+                                                              int naux, double *__restrict__ part) {
+  double a = 0.0, b = 0.0, c = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const double d = D[i];
+    if (J) a = fma(d, J[i], a);
+    if (K) c = fma(d, K[i], c);
+  }
+  if (rho)
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < naux; i += stride)
+      b = fma(rho[i], rho[i], b);
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  __shared__ double red[3][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][warp] = a;
+    red[1][warp] = b;
+    red[2][warp] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+    part[blockIdx.x * 3 + threadIdx.x] = s;
+  }
+}
+
+__global__ void energy_final_kernel(const double *__restrict__ part, int nblocks, double *__restrict__ E) {
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = 0; i < nblocks; ++i) {
+      a += part[3 * i];
+      b += part[3 * i + 1];
+      c += part[3 * i + 2];
+    }
+    E[0] = 0.5 * a;
+    E[1] = 0.5 * b;
+    E[2] = -0.5 * c;
+  }
+}
+
+}  // namespace
+
+constexpr int kEnergyBlocks = 296;
+
+cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st) {
+  rho_kernel<<<naux, 256, 0, st>>>(B, D, nao, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st) {
+  const size_t sm = (size_t)naux * sizeof(double);
+  static size_t attr = 48 * 1024;
+  if (sm > attr) {
+    cudaError_t e = cudaFuncSetAttribute(coulomb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = sm;
+  }
+  dim3 grid((nao + 255) / 256, nao);
+  coulomb_kernel<<<grid, 256, sm, st>>>(B, rho, naux, nao, J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const double *D, const double *J, const double *K, const double *rho, int nao, int naux,
+                          double *partials, double *E_dev, cudaStream_t st) {
+  energy_partials_kernel<<<kEnergyBlocks, 256, 0, st>>>(D, J, K, rho, (long long)nao * nao, naux, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  energy_final_kernel<<<1, 32, 0, st>>>(partials, kEnergyBlocks, E_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace df

@@ -1,0 +1,577 @@
+// C ABI of libdf (include/df.h): the context, its workspaces and the build
+// sequences of the DF Coulomb and exchange matrices.
+//
+// Exchange build at s slices (Section 3.2; blocked as Eqs. df-k-blk-1/2):
+//   1. split C per column into s digit planes          (split kernel, HBM)
+//   2. X^T tiles = C^T B^T over the B digit planes     (slice GEMM, tensor cores)
+//   3. split X per (block, mu) row over (P in block, i) (split kernel, HBM)
+//   4. per block K_b = X_b X_b^T on upper tiles        (slice GEMM, tensor cores)
+//   5. K = sum_b K_b in block order, mirrored          (reduce kernel)
+// The FP64 comparison build (nslices = 0) runs the same contractions through
+// cuBLAS DGEMM (strided batched over P) and DSYRK.
+#include "df_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+struct df_ctx {
+  int nao = 0, naux = 0, nocc_max = 0, s_max = 0, nblk = 0;
+  long long ld_nao = 0;    // row stride (elements) of the B and C digit rows
+  long long kb_ld_max = 0; // row stride bound of the X digit rows
+  const double *B = nullptr;
+  bool ready = false;
+  uint16_t *Bd = nullptr;
+  int *eB = nullptr;
+  uint16_t *Cd = nullptr;
+  int *eC = nullptr;
+  double *X = nullptr;
+  uint16_t *Xd = nullptr;
+  int *eX = nullptr;
+  double *Kp = nullptr;
+  double *rho = nullptr;
+  double *epart = nullptr;
+  double *E = nullptr;
+  int *sblk = nullptr;      // device per-block slice counts
+  int *sblk_host = nullptr; // pinned mirror of the last upload
+  int *status = nullptr;
+  int64_t bytes = 0;
+  df_status last = DF_OK;
+  cublasHandle_t cublas = nullptr;
+  // per-phase event timing
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[DF_NPHASES];
+  std::vector<cudaEvent_t> pool;
+  // adaptive controller (Section 3.2)
+  int level = 4, iter = 0, fp64_from = -1;
+  double E_prev = 0.0;
+};
+
+namespace {
+
+using df::kBlock;
+
+df_status record(df_ctx *c, df_status s) {
+  if (c && s != DF_OK && c->last == DF_OK) c->last = s;
+  return s;
+}
+
+df_status cuda_status(df_ctx *c, cudaError_t e) {
+  if (e == cudaSuccess) return DF_OK;
+  if (e == cudaErrorMemoryAllocation) return record(c, DF_ERR_OOM);
+  return record(c, DF_ERR_CUDA);
+}
+
+// Records a start/stop event pair around a phase when profiling is on.
+struct PhaseTimer {
+  df_ctx *c;
+  int phase;
+  cudaStream_t st;
+  cudaEvent_t e1 = nullptr;
+  PhaseTimer(df_ctx *c_, int ph, cudaStream_t s) : c(c_), phase(ph), st(s) {
+    if (c && c->profiling) {
+      cudaEvent_t e0 = take();
+      e1 = take();
+      cudaEventRecord(e0, st);
+      c->ev[phase].push_back({e0, e1});
+    }
+  }
+  ~PhaseTimer() {
+    if (e1) cudaEventRecord(e1, st);
+  }
+  cudaEvent_t take() {
+    if (!c->pool.empty()) {
+      cudaEvent_t e = c->pool.back();
+      c->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+#define DF_TRY(ctx, expr)                          \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return cuda_status(ctx, _e); \
+  } while (0)
+
+template <typename T>
+cudaError_t alloc(df_ctx *c, T **p, size_t count) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
+  if (e == cudaSuccess) c->bytes += (int64_t)bytes;
+  return e;
+}
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Upload per-block slice counts if they changed.
+df_status upload_slices(df_ctx *c, const int *sb, cudaStream_t st) {
+  bool same = true;
+  for (int b = 0; b < c->nblk; ++b) same &= (c->sblk_host[b] == sb[b]);
+  if (same) return DF_OK;
+  DF_TRY(c, cudaStreamSynchronize(st));  // the pinned mirror may still feed an earlier copy
+  for (int b = 0; b < c->nblk; ++b) c->sblk_host[b] = sb[b];
+  DF_TRY(c, cudaMemcpyAsync(c->sblk, c->sblk_host, sizeof(int) * c->nblk, cudaMemcpyHostToDevice, st));
+  return DF_OK;
+}
+
+__global__ void mirror_lower_to_upper(double *K, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j < n && j > i) K[(long long)i * n + j] = K[(long long)j * n + i];
+}
+
+df_status build_K_fp64(df_ctx *c, const double *C, int nocc, double *K, cudaStream_t st) {
+  if (!c->cublas) {
+    if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) return record(c, DF_ERR_CUDA);
+  }
+  if (cublasSetStream(c->cublas, st) != CUBLAS_STATUS_SUCCESS) return record(c, DF_ERR_CUDA);
+  const double one = 1.0, zero = 0.0;
+  const long long ldx = (long long)c->naux * nocc;
+  // Xt[mu][(P, i)] = X[P][mu][i]: per P, the column-major nocc x nao block
+  // C^T B_P lands at Xt + P*nocc with leading dimension naux*nocc.
+  {
+    PhaseTimer t(c, DF_PHASE_GEMM1, st);
+    cublasStatus_t s1 = cublasDgemmStridedBatched(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, nocc, c->nao, c->nao, &one,
+                                                  C, nocc, 0, c->B, c->nao, (long long)c->nao * c->nao, &zero, c->X,
+                                                  (int)ldx, nocc, c->naux);
+    if (s1 != CUBLAS_STATUS_SUCCESS) return record(c, DF_ERR_CUDA);
+  }
+  PhaseTimer t2(c, DF_PHASE_GEMM2, st);
+  cublasStatus_t s2 = cublasDsyrk(c->cublas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, c->nao, (int)ldx, &one, c->X,
+                                  (int)ldx, &zero, K, c->nao);
+  if (s2 != CUBLAS_STATUS_SUCCESS) return record(c, DF_ERR_CUDA);
+  dim3 grid((c->nao + 127) / 128, c->nao);
+  mirror_lower_to_upper<<<grid, 128, 0, st>>>(K, c->nao);
+  DF_TRY(c, cudaGetLastError());
+  return DF_OK;
+}
+
+df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, double *K, df_kstats *stats,
+                           cudaStream_t st) {
+  int smax = 0;
+  for (int b = 0; b < c->nblk; ++b) {
+    if (sb[b] < 1 || sb[b] > c->s_max) return record(c, DF_ERR_ARG);
+    smax = sb[b] > smax ? sb[b] : smax;
+  }
+  df_status s = upload_slices(c, sb, st);
+  if (s != DF_OK) return s;
+  const int nao = c->nao, naux = c->naux;
+  // 1. C -> digit planes [t][i][nu]
+  const long long c_plane = (long long)c->nocc_max * c->ld_nao;
+  {
+    PhaseTimer t(c, DF_PHASE_SPLIT_C, st);
+    DF_TRY(c, df::launch_split_cols_bf16(C, nao, nocc, smax, c->eC, c->Cd, c->ld_nao, c_plane, st));
+  }
+  // 2. X^T = C^T B^T
+  CUtensorMap ta, tb;
+  if (!df::make_tmap_bf16(&ta, c->Cd, nao, nocc, c->s_max, c->ld_nao, c_plane)) return record(c, DF_ERR_CUDA);
+  if (!df::make_tmap_bf16(&tb, c->Bd, nao, (long long)naux * nao, c->s_max, c->ld_nao,
+                          (long long)naux * nao * c->ld_nao))
+    return record(c, DF_ERR_CUDA);
+  df::SgParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.layout = df::kLayoutX;
+  p.mode = df::kModeX;
+  p.nt_m = (nocc + df::kTile - 1) / df::kTile;
+  p.nt_n = (int)(((long long)naux * nao + df::kTile - 1) / df::kTile);
+  p.nunits = p.nt_m * p.nt_n;
+  p.m_valid = nocc;
+  p.n_valid = naux * nao;
+  p.ktiles = (nao + df::kKTile - 1) / df::kKTile;
+  p.nao = nao;
+  p.nocc = nocc;
+  p.nblk = c->nblk;
+  p.naux = naux;
+  p.s_blk = c->sblk;
+  for (int q = 0; q <= 8; ++q) p.shiftT[q] = df::fixed_point_shift(q, (long long)p.ktiles * df::kKTile);
+  p.ea = c->eC;
+  p.eb = c->eB;
+  p.out = c->X;
+  p.out_ld = nocc;
+  p.status = c->status;
+  {
+    PhaseTimer t(c, DF_PHASE_GEMM1, st);
+    DF_TRY(c, df::launch_slice_gemm(p, ta, tb, st));
+  }
+  // 3. X -> per-(block, mu) digit planes
+  const long long kb_ld = round_up((long long)kBlock * nocc, 64);
+  {
+    PhaseTimer t(c, DF_PHASE_SPLIT_X, st);
+    DF_TRY(c, df::launch_split_xblocks(c->X, naux, nao, nocc, smax, c->eX, c->Xd, kb_ld, c->nblk, st));
+  }
+  // 4. per-block K_b on upper tiles
+  CUtensorMap tx;
+  if (!df::make_tmap_bf16(&tx, c->Xd, kb_ld, nao, (long long)c->s_max * c->nblk, kb_ld, (long long)nao * kb_ld))
+    return record(c, DF_ERR_CUDA);
+  df::SgParams q2;
+  std::memset(&q2, 0, sizeof(q2));
+  q2.layout = df::kLayoutKPart;
+  q2.mode = df::kModeKPart;
+  q2.nt_m = q2.nt_n = (nao + df::kTile - 1) / df::kTile;
+  q2.nunits = q2.nt_m * (q2.nt_m + 1) / 2 * c->nblk;
+  q2.m_valid = q2.n_valid = nao;
+  q2.nao = nao;
+  q2.nocc = nocc;
+  q2.nblk = c->nblk;
+  q2.naux = naux;
+  q2.s_blk = c->sblk;
+  for (int q = 0; q <= 8; ++q) q2.shiftT[q] = df::fixed_point_shift(q, kb_ld);
+  q2.ea = c->eX;
+  q2.eb = c->eX;
+  q2.out = c->Kp;
+  q2.out_ld = nao;
+  q2.out_blk = (long long)nao * nao;
+  q2.status = c->status;
+  {
+    PhaseTimer t(c, DF_PHASE_GEMM2, st);
+    DF_TRY(c, df::launch_slice_gemm(q2, tx, tx, st));
+  }
+  // 5. K = sum_b K_b
+  {
+    PhaseTimer t(c, DF_PHASE_REDUCE, st);
+    DF_TRY(c, df::launch_kpart_reduce(c->Kp, nao, c->nblk, K, st));
+  }
+  if (stats) {
+    stats->nblk = c->nblk;
+    for (int b = 0; b < c->nblk && b < 256; ++b) stats->slices[b] = sb[b];
+    stats->recomputed = 0;
+    stats->fallback = 0;
+  }
+  return DF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *df_strerror(df_status s) {
+  switch (s) {
+    case DF_OK: return "ok";
+    case DF_ERR_ARG: return "invalid argument";
+    case DF_ERR_CUDA: return "CUDA or cuBLAS call failed";
+    case DF_ERR_OOM: return "device allocation failed";
+    case DF_ERR_NOT_PD: return "metric not positive definite";
+    case DF_ERR_TIMEOUT: return "bounded device wait ran out";
+    case DF_ERR_TOL: return "result missed its tolerance";
+    case DF_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+int df_level_for(double dE_rel) {
+  if (dE_rel >= 2e-6) return 4;
+  if (dE_rel >= 5e-9) return 3;
+  if (dE_rel >= 2e-11) return 2;
+  if (dE_rel >= 7e-14) return 1;
+  return 0;
+}
+
+int df_level_slices(int level) {
+  // s = ceil((m_emu + 1) / 8) with m_emu = 23, 31, 39, 47 for levels 4..1
+  static const int m_emu[5] = {0, 47, 39, 31, 23};
+  if (level <= 0 || level > 4) return 0;
+  return (m_emu[level] + 1 + 7) / 8;
+}
+
+df_status df_create(df_ctx **out, int nao, int naux, int nocc_max, int s_max) {
+  if (!out || nao <= 0 || naux <= 0 || nocc_max <= 0 || s_max < 1 || s_max > DF_S_MAX) return DF_ERR_ARG;
+  *out = nullptr;
+  df_ctx *c = new (std::nothrow) df_ctx();
+  if (!c) return DF_ERR_OOM;
+  c->nao = nao;
+  c->naux = naux;
+  c->nocc_max = nocc_max;
+  c->s_max = s_max;
+  c->nblk = (naux + kBlock - 1) / kBlock;
+  c->ld_nao = round_up(nao, 8);
+  c->kb_ld_max = round_up((long long)kBlock * nocc_max, 64);
+  const long long rowsB = (long long)naux * nao;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = alloc(c, &c->Bd, (size_t)s_max * rowsB * c->ld_nao);
+  if (e == cudaSuccess) e = alloc(c, &c->eB, (size_t)rowsB);
+  if (e == cudaSuccess) e = alloc(c, &c->Cd, (size_t)s_max * nocc_max * c->ld_nao);
+  if (e == cudaSuccess) e = alloc(c, &c->eC, (size_t)nocc_max);
+  if (e == cudaSuccess) e = alloc(c, &c->X, (size_t)rowsB * nocc_max);
+  if (e == cudaSuccess) e = alloc(c, &c->Xd, (size_t)s_max * c->nblk * nao * c->kb_ld_max);
+  if (e == cudaSuccess) e = alloc(c, &c->eX, (size_t)c->nblk * nao);
+  if (e == cudaSuccess) e = alloc(c, &c->Kp, (size_t)c->nblk * nao * nao);
+  if (e == cudaSuccess) e = alloc(c, &c->rho, (size_t)naux);
+  if (e == cudaSuccess) e = alloc(c, &c->epart, (size_t)3 * 296);
+  if (e == cudaSuccess) e = alloc(c, &c->E, (size_t)4);
+  if (e == cudaSuccess) e = alloc(c, &c->sblk, (size_t)c->nblk);
+  if (e == cudaSuccess) e = alloc(c, &c->status, (size_t)1);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&c->sblk_host), sizeof(int) * c->nblk);
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->sblk, 0, sizeof(int) * c->nblk);
+  if (e == cudaSuccess) std::memset(c->sblk_host, 0, sizeof(int) * c->nblk);
+  if (e != cudaSuccess) {
+    df_status s = e == cudaErrorMemoryAllocation ? DF_ERR_OOM : DF_ERR_CUDA;
+    cudaGetLastError();
+    df_destroy(c);
+    return s;
+  }
+  *out = c;
+  return DF_OK;
+}
+
+void df_destroy(df_ctx *c) {
+  if (!c) return;
+  cudaFree(c->Bd);
+  cudaFree(c->eB);
+  cudaFree(c->Cd);
+  cudaFree(c->eC);
+  cudaFree(c->X);
+  cudaFree(c->Xd);
+  cudaFree(c->eX);
+  cudaFree(c->Kp);
+  cudaFree(c->rho);
+  cudaFree(c->epart);
+  cudaFree(c->E);
+  cudaFree(c->sblk);
+  cudaFree(c->status);
+  if (c->sblk_host) cudaFreeHost(c->sblk_host);
+  for (int ph = 0; ph < DF_NPHASES; ++ph)
+    for (auto &pr : c->ev[ph]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->cublas) cublasDestroy(c->cublas);
+  delete c;
+}
+
+int64_t df_workspace_bytes(const df_ctx *c) { return c ? c->bytes : 0; }
+
+df_status df_set_profiling(df_ctx *c, int on) {
+  if (!c) return DF_ERR_ARG;
+  c->profiling = on != 0;
+  return DF_OK;
+}
+
+df_status df_phase_times(df_ctx *c, double *ms, int *count) {
+  if (!c || !ms || !count) return DF_ERR_ARG;
+  df_status rs = DF_OK;
+  for (int ph = 0; ph < DF_NPHASES; ++ph) {
+    double total = 0.0;
+    for (auto &pr : c->ev[ph]) {
+      float t = 0.f;
+      if (cudaEventSynchronize(pr.second) != cudaSuccess || cudaEventElapsedTime(&t, pr.first, pr.second) != cudaSuccess)
+        rs = record(c, DF_ERR_CUDA);
+      total += t;
+      c->pool.push_back(pr.first);
+      c->pool.push_back(pr.second);
+    }
+    ms[ph] = total;
+    count[ph] = (int)c->ev[ph].size();
+    c->ev[ph].clear();
+  }
+  return rs;
+}
+
+df_status df_last_error(const df_ctx *c) { return c ? c->last : DF_ERR_ARG; }
+
+df_status df_setup(df_ctx *c, const double *B_dev, void *stream) {
+  if (!c || !B_dev) return record(c, DF_ERR_ARG);
+  cudaStream_t st = as_stream(stream);
+  c->B = B_dev;
+  const long long rows = (long long)c->naux * c->nao;
+  DF_TRY(c, df::launch_split_rows_bf16(B_dev, rows, c->nao, c->nao, c->s_max, c->eB, c->Bd, c->ld_nao,
+                                       rows * c->ld_nao, st));
+  c->ready = true;
+  return DF_OK;
+}
+
+df_status df_build_J(df_ctx *c, const double *D, double *J, double *rho, void *stream) {
+  if (!c || !D || !J) return record(c, DF_ERR_ARG);
+  if (!c->ready) return record(c, DF_ERR_STATE);
+  cudaStream_t st = as_stream(stream);
+  double *r = rho ? rho : c->rho;
+  {
+    PhaseTimer t(c, DF_PHASE_RHO, st);
+    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, r, st));
+  }
+  {
+    PhaseTimer t(c, DF_PHASE_COULOMB, st);
+    DF_TRY(c, df::launch_coulomb(c->B, r, c->naux, c->nao, J, st));
+  }
+  if (rho && rho != c->rho)
+    DF_TRY(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * c->naux, cudaMemcpyDeviceToDevice, st));
+  return DF_OK;
+}
+
+df_status df_build_K(df_ctx *c, const double *C, int nocc, int nslices, double *K, df_kstats *stats, void *stream) {
+  if (!c || !C || !K || nocc <= 0 || nocc > c->nocc_max || nslices < 0 || nslices > c->s_max)
+    return record(c, DF_ERR_ARG);
+  if (!c->ready) return record(c, DF_ERR_STATE);
+  cudaStream_t st = as_stream(stream);
+  if (nslices == 0) {
+    df_status s = build_K_fp64(c, C, nocc, K, st);
+    if (stats && s == DF_OK) {
+      stats->nblk = c->nblk;
+      for (int b = 0; b < c->nblk && b < 256; ++b) stats->slices[b] = 0;
+      stats->recomputed = 0;
+      stats->fallback = 1;
+    }
+    return s;
+  }
+  int sb[4096];
+  if (c->nblk > 4096) return record(c, DF_ERR_ARG);
+  for (int b = 0; b < c->nblk; ++b) sb[b] = nslices;
+  return build_K_emulated(c, C, nocc, sb, K, stats, st);
+}
+
+df_status df_build_K_blocks(df_ctx *c, const double *C, int nocc, const int *slices, double *K, df_kstats *stats,
+                            void *stream) {
+  if (!c || !C || !K || !slices || nocc <= 0 || nocc > c->nocc_max) return record(c, DF_ERR_ARG);
+  if (!c->ready) return record(c, DF_ERR_STATE);
+  return build_K_emulated(c, C, nocc, slices, K, stats, as_stream(stream));
+}
+
+df_status df_energy(df_ctx *c, const double *D, const double *J, const double *K, const double *rho, double *E_host,
+                    void *stream) {
+  if (!c || !D || !E_host) return record(c, DF_ERR_ARG);
+  cudaStream_t st = as_stream(stream);
+  const double *r = rho ? rho : c->rho;
+  {
+    PhaseTimer t(c, DF_PHASE_ENERGY, st);
+    DF_TRY(c, df::launch_energy(D, J, K, r, c->nao, c->naux, c->epart, c->E, st));
+  }
+  DF_TRY(c, cudaMemcpyAsync(E_host, c->E, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DF_TRY(c, cudaStreamSynchronize(st));
+  return DF_OK;
+}
+
+df_status df_adaptive_reset(df_ctx *c, int fp64_from_level) {
+  if (!c) return DF_ERR_ARG;
+  c->level = 4;
+  c->iter = 0;
+  c->E_prev = 0.0;
+  c->fp64_from = fp64_from_level;
+  return DF_OK;
+}
+
+df_status df_adaptive_next(df_ctx *c, double energy, int *level_out, int *nslices_out) {
+  if (!c || !level_out || !nslices_out) return DF_ERR_ARG;
+  if (c->iter > 0 && energy != 0.0) {
+    const double dE = std::fabs((energy - c->E_prev) / energy);
+    const int lv = df_level_for(dE);
+    if (lv < c->level) c->level = lv;  // precision never drops
+  }
+  c->E_prev = energy;
+  c->iter += 1;
+  *level_out = c->level;
+  const bool fp64 = c->level == 0 || (c->fp64_from >= 0 && c->level <= c->fp64_from);
+  *nslices_out = fp64 ? 0 : df_level_slices(c->level);
+  return DF_OK;
+}
+
+df_status df_sync_status(df_ctx *c, void *stream) {
+  if (!c) return DF_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  int h = 0;
+  DF_TRY(c, cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DF_TRY(c, cudaStreamSynchronize(st));
+  if (h) {
+    DF_TRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), st));
+    return record(c, DF_ERR_TIMEOUT);
+  }
+  return DF_OK;
+}
+
+df_status df_split_int8(const double *A, int rows, int cols, int ld, int nslices, int32_t *exps, int8_t *digits,
+                        void *stream) {
+  if (!A || !exps || !digits || rows < 0 || cols < 0 || ld < cols || nslices < 1 || nslices > DF_S_MAX)
+    return DF_ERR_ARG;
+  cudaError_t e = df::launch_split_rows_int8(A, rows, cols, ld, nslices, exps, digits, as_stream(stream));
+  return e == cudaSuccess ? DF_OK : DF_ERR_CUDA;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Shared driver of df_slice_products / df_emulated_gemm: split both operands
+// into BF16 planes in scratch memory, run the slice GEMM, free the scratch.
+df_status grid_gemm(const double *A, const double *B, int M, int N, int K, int s, int mode, int64_t *raw,
+                    double *out, int32_t *ea_out, int32_t *eb_out, cudaStream_t st) {
+  if (!A || !B || M <= 0 || N <= 0 || K <= 0 || s < 1 || s > DF_S_MAX) return DF_ERR_ARG;
+  const long long ld = round_up(K, 8);
+  uint16_t *Ad = nullptr, *Bd = nullptr;
+  int *ea = nullptr, *eb = nullptr, *status = nullptr;
+  df_status rs = DF_OK;
+  cudaError_t e = cudaMalloc(&Ad, sizeof(uint16_t) * (size_t)s * M * ld);
+  if (e == cudaSuccess) e = cudaMalloc(&Bd, sizeof(uint16_t) * (size_t)s * N * ld);
+  if (e == cudaSuccess) e = cudaMalloc(&ea, sizeof(int) * M);
+  if (e == cudaSuccess) e = cudaMalloc(&eb, sizeof(int) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = df::launch_split_rows_bf16(A, M, K, K, s, ea, Ad, ld, (long long)M * ld, st);
+  if (e == cudaSuccess) e = df::launch_split_rows_bf16(B, N, K, K, s, eb, Bd, ld, (long long)N * ld, st);
+  if (e == cudaSuccess) {
+    CUtensorMap ta, tb;
+    if (!df::make_tmap_bf16(&ta, Ad, K, M, s, ld, (long long)M * ld) ||
+        !df::make_tmap_bf16(&tb, Bd, K, N, s, ld, (long long)N * ld)) {
+      rs = DF_ERR_CUDA;
+    } else {
+      df::SgParams p;
+      std::memset(&p, 0, sizeof(p));
+      p.layout = df::kLayoutGrid;
+      p.mode = mode;
+      p.nt_m = (M + df::kTile - 1) / df::kTile;
+      p.nt_n = (N + df::kTile - 1) / df::kTile;
+      p.nunits = p.nt_m * p.nt_n;
+      p.m_valid = M;
+      p.n_valid = N;
+      p.ktiles = (K + df::kKTile - 1) / df::kKTile;
+      p.s_fixed = s;
+      for (int q = 0; q <= 8; ++q) p.shiftT[q] = df::fixed_point_shift(q, (long long)p.ktiles * df::kKTile);
+      p.ea = ea;
+      p.eb = eb;
+      p.out = out;
+      p.out_ld = N;
+      p.raw = reinterpret_cast<long long *>(raw);
+      p.status = status;
+      e = df::launch_slice_gemm(p, ta, tb, st);
+    }
+  }
+  int h = 0;
+  if (e == cudaSuccess && rs == DF_OK) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && rs == DF_OK && ea_out) e = cudaMemcpyAsync(ea_out, ea, sizeof(int) * M, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && rs == DF_OK && eb_out) e = cudaMemcpyAsync(eb_out, eb, sizeof(int) * N, cudaMemcpyDeviceToDevice, st);
+  cudaError_t es = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = es;
+  cudaFree(Ad);
+  cudaFree(Bd);
+  cudaFree(ea);
+  cudaFree(eb);
+  cudaFree(status);
+  if (rs != DF_OK) return rs;
+  if (e != cudaSuccess) return DF_ERR_CUDA;
+  return h ? DF_ERR_TIMEOUT : DF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+df_status df_slice_products(const double *A, const double *B, int M, int N, int K, int nslices, int64_t *S,
+                            int32_t *ea, int32_t *eb, void *stream) {
+  if (!S) return DF_ERR_ARG;
+  return grid_gemm(A, B, M, N, K, nslices, df::kModeRaw, S, nullptr, ea, eb, as_stream(stream));
+}
+
+df_status df_emulated_gemm(const double *A, const double *B, int M, int N, int K, int nslices, double *out,
+                           void *stream) {
+  if (!out) return DF_ERR_ARG;
+  return grid_gemm(A, B, M, N, K, nslices, df::kModeGemm, nullptr, out, nullptr, nullptr, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Internal declarations of libdf: the context, the kernel launchers and the
+// slice-GEMM work description.  Not part of the public ABI (include/df.h).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/df.h"
+#include "df_device.cuh"
+
+namespace df {
+
+constexpr int kTile = 128;       // output tile edge of the slice GEMM
+constexpr int kKTile = 64;       // K elements per pipeline stage (128 bytes of bf16)
+constexpr int kMaxChunk = 1024;  // products per exact FP32 accumulation chunk
+
+// Epilogue modes of the slice GEMM.
+enum SgMode : int {
+  kModeX = 0,       // first exchange GEMM: X[n*ld + m] (transposed tile of X^T = C^T B^T)
+  kModeKPart = 1,   // second exchange GEMM: per-block partial K, out[b*blk + n*ld + m]
+  kModeRaw = 2,     // exact S_g per group: raw[(g*n_valid + n)*m_valid + m]
+  kModeGemm = 3,    // generic emulated product: out[m*ld + n]
+};
+
+// How the persistent kernel turns a unit index into a tile.
+enum SgLayout : int {
+  kLayoutGrid = 0,   // u -> (m_tile = u % nt_m, n_tile = u / nt_m), planes az = t, bz = t
+  kLayoutX = 1,      // first exchange GEMM: n rows are (P, mu); block = n0 / (128 nao)
+  kLayoutKPart = 2,  // second exchange GEMM: u -> (upper tile pair, block)
+};
+
+struct SgParams {
+  int layout, mode;
+  int nunits;
+  int nt_m, nt_n;           // tiles along m and n
+  int m_valid, n_valid;     // rows of the A side and of the B side that exist
+  int ktiles;               // K tiles (64 wide) for kLayoutGrid / kLayoutX
+  int s_fixed;              // slice count for kLayoutGrid
+  int nao, nocc, nblk, naux;
+  const int *s_blk;         // per-block slice counts (kLayoutX, kLayoutKPart)
+  int shiftT[9];            // truncation T of the fixed-point sum, indexed by s (0..8)
+  const int *ea;            // A-side row exponents
+  const int *eb;            // B-side row exponents
+  long long out_ld;
+  long long out_blk;
+  double *out;
+  long long *raw;
+  int *status;              // device status word (DF_ERR_TIMEOUT bits)
+};
+
+struct Ctx;
+
+// Kernel launchers (split.cu, slicegemm.cu, coulomb.cu).
+cudaError_t launch_split_rows_bf16(const double *A, long long rows, int cols, long long ld, int nslices,
+                                   int *exps, uint16_t *digits, long long dld, long long plane_stride,
+                                   cudaStream_t st);
+cudaError_t launch_split_rows_int8(const double *A, int rows, int cols, int ld, int nslices, int *exps,
+                                   int8_t *digits, cudaStream_t st);
+cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int nslices, int *exps,
+                                   uint16_t *digits, long long dld, long long plane_stride, cudaStream_t st);
+cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, int nslices, int *eX,
+                                 uint16_t *Xd, long long kb_ld, int nblk, cudaStream_t st);
+cudaError_t launch_kpart_reduce(const double *Kp, int nao, int nblk, double *K, cudaStream_t st);
+
+// Encode a 3D bf16 tensor map {k, rows, planes} with a 64 x 128 x 1 box, 128B swizzle.
+bool make_tmap_bf16(CUtensorMap *map, const void *base, long long k, long long rows, long long planes,
+                    long long row_stride_elems, long long plane_stride_elems);
+
+cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb,
+                              cudaStream_t st);
+int slice_gemm_grid(int nunits);
+int fixed_point_shift(int s, long long k);
+
+cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st);
+cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st);
+cudaError_t launch_energy(const double *D, const double *J, const double *K, const double *rho, int nao,
+                          int naux, double *partials, double *E_dev, cudaStream_t st);
+
+}  // namespace df

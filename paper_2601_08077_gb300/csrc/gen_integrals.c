@@ -15,6 +15,7 @@
  */
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 static const double kPi = 3.14159265358979323846;
 
@@ -26,36 +27,53 @@ static double boys0(double t) {
 
 static double norm_s(double a) { return pow(2.0 * a / kPi, 0.75); }
 
-/* out[P][mu][nu], row-major, for nao AO and naux auxiliary primitives. */
+/* out[P][mu][nu], row-major, for nao AO and naux auxiliary primitives.
+ * The Gaussian-product quantities of every AO pair are formed once; the loop
+ * over P then only evaluates the Boys factor. */
 void gen_int3c(int nao, int naux, const double *ao_xyz, const double *ao_exp,
                const double *aux_xyz, const double *aux_exp, double *out) {
   const double two_pi52 = 2.0 * pow(kPi, 2.5);
+  const size_t npair = (size_t)nao * (nao + 1) / 2;
+  double *pp = (double *)malloc(sizeof(double) * npair * 5);
+  int *pm = (int *)malloc(sizeof(int) * npair * 2);
+  size_t q = 0;
+  for (int m = 0; m < nao; ++m) {
+    const double a = ao_exp[m];
+    const double ax = ao_xyz[3 * m], ay = ao_xyz[3 * m + 1], az = ao_xyz[3 * m + 2];
+    for (int n = 0; n <= m; ++n, ++q) {
+      const double b = ao_exp[n];
+      const double bx = ao_xyz[3 * n], by = ao_xyz[3 * n + 1], bz = ao_xyz[3 * n + 2];
+      const double p = a + b;
+      const double dx = ax - bx, dy = ay - by, dz = az - bz;
+      const double kab = exp(-a * b / p * (dx * dx + dy * dy + dz * dz));
+      pp[5 * q + 0] = p;
+      pp[5 * q + 1] = (a * ax + b * bx) / p;
+      pp[5 * q + 2] = (a * ay + b * by) / p;
+      pp[5 * q + 3] = (a * az + b * bz) / p;
+      pp[5 * q + 4] = norm_s(a) * norm_s(b) * kab;
+      pm[2 * q] = m;
+      pm[2 * q + 1] = n;
+    }
+  }
 #pragma omp parallel for schedule(dynamic, 1)
   for (int P = 0; P < naux; ++P) {
     const double g = aux_exp[P];
     const double cx = aux_xyz[3 * P], cy = aux_xyz[3 * P + 1], cz = aux_xyz[3 * P + 2];
     const double nc = norm_s(g);
     double *row = out + (size_t)P * nao * nao;
-    for (int m = 0; m < nao; ++m) {
-      const double a = ao_exp[m];
-      const double ax = ao_xyz[3 * m], ay = ao_xyz[3 * m + 1], az = ao_xyz[3 * m + 2];
-      const double na = norm_s(a);
-      for (int n = 0; n <= m; ++n) {
-        const double b = ao_exp[n];
-        const double bx = ao_xyz[3 * n], by = ao_xyz[3 * n + 1], bz = ao_xyz[3 * n + 2];
-        const double p = a + b;
-        const double dx = ax - bx, dy = ay - by, dz = az - bz;
-        const double kab = exp(-a * b / p * (dx * dx + dy * dy + dz * dz));
-        const double px = (a * ax + b * bx) / p, py = (a * ay + b * by) / p,
-                     pz = (a * az + b * bz) / p;
-        const double ex = px - cx, ey = py - cy, ez = pz - cz;
-        const double t = g * p / (g + p) * (ex * ex + ey * ey + ez * ez);
-        const double v = nc * na * norm_s(b) * kab * two_pi52 / (g * p * sqrt(g + p)) * boys0(t);
-        row[(size_t)m * nao + n] = v;
-        row[(size_t)n * nao + m] = v;
-      }
+    for (size_t k = 0; k < npair; ++k) {
+      const double *e = pp + 5 * k;
+      const double p = e[0];
+      const double ex = e[1] - cx, ey = e[2] - cy, ez = e[3] - cz;
+      const double t = g * p / (g + p) * (ex * ex + ey * ey + ez * ez);
+      const double v = nc * e[4] * two_pi52 / (g * p * sqrt(g + p)) * boys0(t);
+      const int m = pm[2 * k], n = pm[2 * k + 1];
+      row[(size_t)m * nao + n] = v;
+      row[(size_t)n * nao + m] = v;
     }
   }
+  free(pp);
+  free(pm);
 }
 
 /* out[P][Q], the Coulomb metric of the auxiliary primitives. */

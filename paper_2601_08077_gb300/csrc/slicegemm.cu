@@ -1,0 +1,523 @@
+// Slice GEMM on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+//
+// Computes, for an output tile of 128 (A-side rows) x 128 (B-side rows), the
+// exact slice-pair sums of Section 3.2
+//
+//     S_g = sum_{t+u=g} A_t B_u^T,   g = 0 .. s-1,
+//
+// where A_t, B_u are INT8 digit planes (row-major, K contiguous), and folds
+// them into the fixed-point value R = sum_g 2^(8(s-1-g)) S_g, which the
+// epilogue turns into FP64 with the per-row / per-column power-of-two scales.
+//
+// GB300 mapping.  ptxas rejects tcgen05 .kind::i8 on sm_103a, so the digits
+// are stored as BF16 (every integer in [-256, 256] is exact in BF16) and run
+// through tcgen05.mma .kind::f16 with FP32 accumulators in TMEM.  A product of
+// two digits is at most 2^14 in magnitude, so an accumulation of at most 1024
+// products stays within 2^24 and is exact in FP32; the MMA warp therefore
+// closes an accumulator "chunk" every 1024 products (16 pipeline stages) and
+// the epilogue warps fold it exactly into an int64 running sum that also
+// lives in TMEM.  Two FP32 accumulator buffers (columns 0-255) let the tensor
+// core fill one while the epilogue drains the other; the int64 sums use
+// columns 256-511 (two 32-bit columns per output column).
+//
+// Warp roles (192 threads, one CTA per SM, persistent over work units):
+//   warp 0      TMA producer: 128x64 BF16 boxes of A_t and B_u, 128B swizzle,
+//               into a 6-stage ring (32 KB per stage) guarded by mbarriers;
+//   warp 1      TMEM allocation and the single-thread tcgen05.mma issuer;
+//   warps 2..5  epilogue; warp w reads TMEM lanes 32*(w%4)..+31 (tile rows).
+//
+// Every mbarrier wait is bounded (4 s of wall clock); a wait that runs out
+// sets a shared abort flag and bit 1 of the device status word, every role
+// leaves its loop, the producer waits (bounded) for its copies in flight, the
+// MMA issuer waits (bounded) for its MMAs, and the TMEM is freed.
+#include "df_internal.h"
+
+#include <cstdio>
+
+namespace df {
+
+namespace {
+
+constexpr int kStages = 6;
+constexpr int kTileBytes = kTile * kKTile * 2;  // 16 KB of BF16
+constexpr int kStageBytes = 2 * kTileBytes;     // A tile + B tile
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kRCol = 256;
+constexpr int kChunkStages = kMaxChunk / kKTile;  // 16 stages = 1024 products
+constexpr uint64_t kTimeoutNs = 4000000000ull;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*alignment slack*/;
+
+// BF16 x BF16 -> FP32, both operands K-major, M = N = 128 (instruction
+// descriptor of tcgen05.mma .kind::f16: D fmt bits 4-5, A fmt 7-9, B fmt
+// 10-12, N>>3 at 17-22, M>>4 at 24-28).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) |
+                            ((uint32_t)(kTile >> 4) << 24);
+
+struct Unit {
+  int m0, n0, az0, azs, bz0, bzs, ktiles, s, blk;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait.  Returns false if the CTA is aborting or the wait ran out.
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                             int *status, bool honour_abort = true) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (honour_abort && *abort_flag) return false;
+    if (globaltimer_ns() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      atomicOr(status, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core
+// groups 1024 bytes apart (SBO), descriptor version 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
+  Unit w;
+  if (p.layout == kLayoutKPart) {
+    const int npairs = p.nt_m * (p.nt_m + 1) / 2;
+    const int pr = u % npairs;
+    const int b = u / npairs;
+    int i = 0, rem = pr;
+    while (rem >= p.nt_m - i) {
+      rem -= p.nt_m - i;
+      ++i;
+    }
+    w.m0 = i * kTile;
+    w.n0 = (i + rem) * kTile;
+    w.az0 = b;
+    w.azs = p.nblk;
+    w.bz0 = b;
+    w.bzs = p.nblk;
+    const int nP = min(kBlock, p.naux - b * kBlock);
+    w.ktiles = (nP * p.nocc + kKTile - 1) / kKTile;
+    w.s = p.s_blk[b];
+    w.blk = b;
+  } else {
+    const int mt = u % p.nt_m;
+    const int nt = u / p.nt_m;
+    w.m0 = mt * kTile;
+    w.n0 = nt * kTile;
+    w.az0 = 0;
+    w.azs = 1;
+    w.bz0 = 0;
+    w.bzs = 1;
+    w.ktiles = p.ktiles;
+    if (p.layout == kLayoutX) {
+      w.blk = (int)((long long)w.n0 / ((long long)kBlock * p.nao));
+      w.s = p.s_blk[w.blk];
+    } else {
+      w.blk = 0;
+      w.s = p.s_fixed;
+    }
+  }
+  return w;
+}
+
+// Epilogue store of 16 consecutive output columns n0c..n0c+15 of row m.
+__device__ __forceinline__ void store16(const SgParams &p, const Unit &w, int m, int n0c, int g,
+                                        const uint32_t (&lo)[16], const uint32_t (&hi)[16], int kexp_base,
+                                        int ea_m) {
+  if (m >= p.m_valid) return;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int n = n0c + j;
+    if (n >= p.n_valid) break;
+    const long long R = (long long)(((uint64_t)hi[j] << 32) | (uint64_t)lo[j]);
+    if (p.mode == kModeRaw) {
+      p.raw[((long long)g * p.n_valid + n) * p.m_valid + m] = R;
+    } else if (p.mode == kModeX) {
+      const double v = ldexp_i64(R, kexp_base + ea_m + p.eb[n]);
+      p.out[(long long)n * p.out_ld + m] = v;
+    } else if (p.mode == kModeKPart) {
+      const double v = ldexp_i64(R, kexp_base + ea_m + p.eb[(long long)w.blk * p.nao + n]);
+      p.out[(long long)w.blk * p.out_blk + (long long)n * p.out_ld + m] = v;
+    } else {
+      const double v = ldexp_i64(R, kexp_base + ea_m + p.eb[n]);
+      p.out[(long long)m * p.out_ld + n] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
+                      const SgParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+  uint64_t *empty = full + kStages;
+  uint64_t *acc_full = empty + kStages;
+  uint64_t *acc_empty = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
+        const Unit w = decode_unit(p, u);
+        for (int g = 0; g < w.s && ok; ++g) {
+          for (int t = 0; t <= g && ok; ++t) {
+            for (int kt = 0; kt < w.ktiles; ++kt) {
+              const uint32_t stage = it % kStages;
+              const uint32_t ph = (it / kStages) & 1;
+              if (!wait_bounded(&empty[stage], ph ^ 1, abort_flag, p.status)) {
+                ok = false;
+                break;
+              }
+              uint8_t *sa = smem + stage * kStageBytes;
+              uint8_t *sb = sa + kTileBytes;
+              mbar_expect_tx(&full[stage], kStageBytes);
+              tma_load_3d(sa, &tmap_a, &full[stage], kt * kKTile, w.m0, w.az0 + t * w.azs);
+              tma_load_3d(sb, &tmap_b, &full[stage], kt * kKTile, w.n0, w.bz0 + (g - t) * w.bzs);
+              ++it;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA goes away
+        const uint32_t first = it > (uint32_t)kStages ? it - kStages : 0u;
+        for (uint32_t j = first; j < it; ++j)
+          wait_bounded(&full[j % kStages], (j / kStages) & 1, abort_flag, p.status, false);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    uint32_t it = 0, qc = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
+      const Unit w = decode_unit(p, u);
+      for (int g = 0; g < w.s && ok; ++g) {
+        int chunk_pos = 0;
+        for (int t = 0; t <= g && ok; ++t) {
+          for (int kt = 0; kt < w.ktiles; ++kt) {
+            const uint32_t stage = it % kStages;
+            const uint32_t ph = (it / kStages) & 1;
+            const uint32_t buf = qc & 1;
+            if (chunk_pos == 0) {
+              if (!wait_bounded(&acc_empty[buf], ((qc >> 1) & 1) ^ 1, abort_flag, p.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
+            if (!wait_bounded(&full[stage], ph, abort_flag, p.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            if (lane == 0) {
+              const uint32_t sa = smem_u32(smem + stage * kStageBytes);
+              const uint32_t sb = sa + kTileBytes;
+              const uint32_t dt = tmem_base + buf * kTile;
+#pragma unroll
+              for (int k = 0; k < kKTile / 16; ++k)
+                umma_bf16(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), kIdesc,
+                          (chunk_pos > 0 || k > 0) ? 1u : 0u);
+              umma_commit(&empty[stage]);
+            }
+            __syncwarp();
+            ++it;
+            ++chunk_pos;
+            const bool group_end = (t == g) && (kt == w.ktiles - 1);
+            if (chunk_pos == kChunkStages || group_end) {
+              if (lane == 0) umma_commit(&acc_full[buf]);
+              __syncwarp();
+              ++qc;
+              chunk_pos = 0;
+            }
+          }
+        }
+      }
+    }
+    if (!ok && lane == 0) {
+      // wait for the MMAs already issued before the TMEM is released
+      uint64_t *done = &acc_full[qc & 1];
+      umma_commit(done);
+      wait_bounded(done, (qc >> 1) & 1, abort_flag, p.status, false);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    const uint32_t taddr_lane = tmem_base + ((uint32_t)(quad * 32) << 16);
+    uint32_t qc = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
+      const Unit w = decode_unit(p, u);
+      const int s = w.s;
+      const int T = p.mode == kModeRaw ? 0 : p.shiftT[s];
+      const int m = w.m0 + row;
+      int ea_m = 0;
+      if (p.mode != kModeRaw && m < p.m_valid)
+        ea_m = p.mode == kModeKPart ? p.ea[(long long)w.blk * p.nao + m] : p.ea[m];
+      const int kexp_base = -14 - 8 * (s - 1) + T;
+      bool first = true;
+      for (int g = 0; g < s && ok; ++g) {
+        const int nst = (g + 1) * w.ktiles;
+        const int nch = (nst + kChunkStages - 1) / kChunkStages;
+        const int sh = p.mode == kModeRaw ? 0 : 8 * (s - 1 - g) - T;
+        for (int c = 0; c < nch; ++c) {
+          const uint32_t buf = qc & 1;
+          if (!wait_bounded(&acc_full[buf], (qc >> 1) & 1, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll 1
+          for (int cb = 0; cb < kTile / 16; ++cb) {
+            uint32_t a[16], lo[16], hi[16];
+            tmem_ld16(taddr_lane + buf * kTile + cb * 16, a);
+            if (!first) {
+              tmem_ld16(taddr_lane + kRCol + cb * 32, lo);
+              tmem_ld16(taddr_lane + kRCol + cb * 32 + 16, hi);
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const long long v = (long long)__float2int_rz(__uint_as_float(a[j]));
+              long long add;
+              if (sh >= 0)
+                add = v << sh;
+              else
+                add = (v + (1ll << (-sh - 1))) >> (-sh);
+              long long R = first ? 0ll : (long long)(((uint64_t)hi[j] << 32) | (uint64_t)lo[j]);
+              R += add;
+              lo[j] = (uint32_t)((uint64_t)R & 0xFFFFFFFFull);
+              hi[j] = (uint32_t)((uint64_t)R >> 32);
+            }
+            tmem_st16(taddr_lane + kRCol + cb * 32, lo);
+            tmem_st16(taddr_lane + kRCol + cb * 32 + 16, hi);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[buf]);
+          ++qc;
+          first = false;
+          const bool last_of_group = (c == nch - 1);
+          if (last_of_group && (p.mode == kModeRaw || g == s - 1)) {
+            // write the finished tile (per group in raw mode)
+#pragma unroll 1
+            for (int cb = 0; cb < kTile / 16; ++cb) {
+              uint32_t lo[16], hi[16];
+              tmem_ld16(taddr_lane + kRCol + cb * 32, lo);
+              tmem_ld16(taddr_lane + kRCol + cb * 32 + 16, hi);
+              tmem_wait_ld();
+              store16(p, w, m, w.n0 + cb * 16, g, lo, hi, kexp_base, ea_m);
+            }
+            if (p.mode == kModeRaw) first = true;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                    CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                    CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled get_encode_fn() {
+  static PFN_encodeTiled fn = nullptr;
+  if (!fn) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled>(ptr);
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool make_tmap_bf16(CUtensorMap *map, const void *base, long long k, long long rows, long long planes,
+                    long long row_stride_elems, long long plane_stride_elems) {
+  PFN_encodeTiled enc = get_encode_fn();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_stride_elems * 2) % 16 || (plane_stride_elems * 2) % 16)
+    return false;
+  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(row_stride_elems * 2), (cuuint64_t)(plane_stride_elems * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)kKTile, (cuuint32_t)kTile, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Truncation T of the int64 fixed-point sum: |R| <= sum_g (g+1) K 2^14
+// 2^(8(s-1-g)) must stay below 2^61 after dropping T low bits.  T = 0 (exact)
+// whenever that bound allows it.
+int fixed_point_shift(int s, long long k) {
+  if (s <= 0) return 0;
+  long double bound = 0.0L;
+  for (int g = 0; g < s; ++g) bound += (long double)(g + 1) * (long double)k * 16384.0L * ldexpl(1.0L, 8 * (s - 1 - g));
+  int bits = 0;
+  while (ldexpl(1.0L, bits) < bound) ++bits;
+  return bits > 61 ? bits - 61 : 0;
+}
+
+int slice_gemm_grid(int nunits) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  return nunits < nsm ? nunits : nsm;
+}
+
+cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
+  if (p.nunits <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  slice_gemm_kernel<<<slice_gemm_grid(p.nunits), kThreads, kSmemBytes, st>>>(ta, tb, p);
+  return cudaGetLastError();
+}
+
+}  // namespace df

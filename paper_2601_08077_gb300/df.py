@@ -1,0 +1,230 @@
+"""Thin ctypes binding of libdf (include/df.h): argument marshalling only.
+
+Every step of the J/K builds runs in the CUDA library; this module only turns
+torch CUDA tensors into device pointers and the current stream into a
+``cudaStream_t``.  There is no CPU fallback: if ``_build/libdf.so`` is missing
+or CUDA is unavailable, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdf.so")
+
+S_MAX = 8
+AUX_BLOCK = 128
+PHASES = ("split_C", "gemm1", "split_X", "gemm2", "reduce", "rho", "coulomb", "energy")
+
+_STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA or cuBLAS call failed", -3: "device allocation failed",
+           -4: "metric not positive definite", -5: "bounded device wait ran out", -6: "result missed its tolerance",
+           -7: "call out of order"}
+
+
+class DFError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__("%s: %s (status %d)" % (where, _STATUS.get(status, "unknown"), status))
+        self.status = status
+
+
+class KStats(ctypes.Structure):
+    _fields_ = [("nblk", ctypes.c_int), ("slices", ctypes.c_int * 256), ("recomputed", ctypes.c_int),
+                ("fallback", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdf; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdf is not built (%s missing): run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        L.df_create.argtypes = [pp, I, I, I, I]
+        L.df_destroy.argtypes = [P]
+        L.df_destroy.restype = None
+        L.df_setup.argtypes = [P, P, V]
+        L.df_build_J.argtypes = [P, P, P, P, V]
+        L.df_build_K.argtypes = [P, P, I, I, P, ctypes.POINTER(KStats), V]
+        L.df_build_K_blocks.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(KStats), V]
+        L.df_energy.argtypes = [P, P, P, P, P, ctypes.POINTER(ctypes.c_double), V]
+        L.df_split_int8.argtypes = [P, I, I, I, I, P, P, V]
+        L.df_slice_products.argtypes = [P, P, I, I, I, I, P, P, P, V]
+        L.df_emulated_gemm.argtypes = [P, P, I, I, I, I, P, V]
+        L.df_level_for.argtypes = [D]
+        L.df_level_for.restype = I
+        L.df_level_slices.argtypes = [I]
+        L.df_level_slices.restype = I
+        L.df_adaptive_reset.argtypes = [P, I]
+        L.df_adaptive_next.argtypes = [P, D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.df_sync_status.argtypes = [P, V]
+        L.df_last_error.argtypes = [P]
+        L.df_strerror.argtypes = [I]
+        L.df_strerror.restype = ctypes.c_char_p
+        L.df_set_profiling.argtypes = [P, I]
+        L.df_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        L.df_workspace_bytes.argtypes = [P]
+        L.df_workspace_bytes.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise DFError(status, where)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _f64(t):
+    if t.dtype != torch.float64:
+        raise ValueError("expected float64, got %s" % t.dtype)
+    return _ptr(t)
+
+
+def level_for(dE_rel: float) -> int:
+    return lib().df_level_for(float(dE_rel))
+
+
+def level_slices(level: int) -> int:
+    return lib().df_level_slices(int(level))
+
+
+def split_int8(A: torch.Tensor, nslices: int, stream=None):
+    """Row exponents (int32) and INT8 digits [nslices, rows, cols] of a 2-D FP64 tensor."""
+    rows, cols = A.shape
+    exps = torch.empty(rows, dtype=torch.int32, device=A.device)
+    digits = torch.empty((nslices, rows, cols), dtype=torch.int8, device=A.device)
+    _check(lib().df_split_int8(_f64(A), rows, cols, cols, nslices, _ptr(exps), _ptr(digits), _stream(stream)),
+           "df_split_int8")
+    return exps, digits
+
+
+def slice_products(A: torch.Tensor, B: torch.Tensor, nslices: int, stream=None):
+    """Exact S_g = sum_{t+u=g} A_t B_u^T, returned as int64 [nslices, M, N], plus row exponents."""
+    M, K = A.shape
+    N, K2 = B.shape
+    assert K == K2
+    S = torch.empty((nslices, N, M), dtype=torch.int64, device=A.device)
+    ea = torch.empty(M, dtype=torch.int32, device=A.device)
+    eb = torch.empty(N, dtype=torch.int32, device=A.device)
+    _check(lib().df_slice_products(_f64(A), _f64(B), M, N, K, nslices, _ptr(S), _ptr(ea), _ptr(eb),
+                                   _stream(stream)), "df_slice_products")
+    return S.transpose(1, 2), ea, eb
+
+
+def emulated_gemm(A: torch.Tensor, B: torch.Tensor, nslices: int, stream=None):
+    """A @ B^T emulated with nslices INT8 slices per operand."""
+    M, K = A.shape
+    N, _ = B.shape
+    out = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    _check(lib().df_emulated_gemm(_f64(A), _f64(B), M, N, K, nslices, _ptr(out), _stream(stream)),
+           "df_emulated_gemm")
+    return out
+
+
+class Context:
+    """One molecule's DF workspaces on the current CUDA device."""
+
+    def __init__(self, nao: int, naux: int, nocc_max: int, s_max: int = S_MAX):
+        self.nao, self.naux, self.nocc_max, self.s_max = nao, naux, nocc_max, s_max
+        self.nblk = (naux + AUX_BLOCK - 1) // AUX_BLOCK
+        h = ctypes.c_void_p()
+        _check(lib().df_create(ctypes.byref(h), nao, naux, nocc_max, s_max), "df_create")
+        self._h = h
+        self._B = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().df_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().df_workspace_bytes(self._h))
+
+    def setup(self, B: torch.Tensor, stream=None):
+        assert B.shape == (self.naux, self.nao, self.nao)
+        self._B = B  # the library keeps the pointer: keep the tensor alive
+        _check(lib().df_setup(self._h, _f64(B), _stream(stream)), "df_setup")
+
+    def build_J(self, D, J=None, rho=None, stream=None):
+        if J is None:
+            J = torch.empty((self.nao, self.nao), dtype=torch.float64, device=D.device)
+        if rho is None:
+            rho = torch.empty(self.naux, dtype=torch.float64, device=D.device)
+        _check(lib().df_build_J(self._h, _f64(D), _f64(J), _f64(rho), _stream(stream)), "df_build_J")
+        return J, rho
+
+    def build_K(self, C, nslices: int, K=None, stream=None):
+        nocc = C.shape[1]
+        if K is None:
+            K = torch.empty((self.nao, self.nao), dtype=torch.float64, device=C.device)
+        st = KStats()
+        _check(lib().df_build_K(self._h, _f64(C), nocc, int(nslices), _f64(K), ctypes.byref(st), _stream(stream)),
+               "df_build_K")
+        return K, st
+
+    def build_K_blocks(self, C, slices, K=None, stream=None):
+        nocc = C.shape[1]
+        if K is None:
+            K = torch.empty((self.nao, self.nao), dtype=torch.float64, device=C.device)
+        arr = (ctypes.c_int * self.nblk)(*[int(s) for s in slices])
+        st = KStats()
+        _check(lib().df_build_K_blocks(self._h, _f64(C), nocc, arr, _f64(K), ctypes.byref(st), _stream(stream)),
+               "df_build_K_blocks")
+        return K, st
+
+    def energy(self, D, J=None, K=None, rho=None, stream=None):
+        """(1/2 tr DJ, 1/2 rho.rho, -1/2 tr DK); synchronises the stream."""
+        E = (ctypes.c_double * 3)()
+        _check(lib().df_energy(self._h, _f64(D), _ptr(J), _ptr(K), _ptr(rho), E, _stream(stream)), "df_energy")
+        return E[0], E[1], E[2]
+
+    def adaptive_reset(self, fp64_from_level: int = -1):
+        _check(lib().df_adaptive_reset(self._h, int(fp64_from_level)), "df_adaptive_reset")
+
+    def adaptive_next(self, energy: float):
+        lv, ns = ctypes.c_int(), ctypes.c_int()
+        _check(lib().df_adaptive_next(self._h, float(energy), ctypes.byref(lv), ctypes.byref(ns)),
+               "df_adaptive_next")
+        return lv.value, ns.value
+
+    def set_profiling(self, on: bool):
+        _check(lib().df_set_profiling(self._h, 1 if on else 0), "df_set_profiling")
+
+    def phase_times(self):
+        """{phase: (total ms, records)} since the last read (waits for the events)."""
+        ms = (ctypes.c_double * len(PHASES))()
+        cnt = (ctypes.c_int * len(PHASES))()
+        _check(lib().df_phase_times(self._h, ms, cnt), "df_phase_times")
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(PHASES)}
+
+    def sync_status(self, stream=None):
+        _check(lib().df_sync_status(self._h, _stream(stream)), "df_sync_status")

@@ -136,11 +136,17 @@ def metric(mol: Molecule) -> np.ndarray:
 def df_tensor(mol: Molecule) -> np.ndarray:
     """B[P, mu, nu] = sum_Q L^{-1}[P, Q] (Q|mu nu), L L^T = (P|Q) (Eq. cderi)."""
     import scipy.linalg as sl
+    from scipy.linalg.blas import dtrsm
     V = metric(mol)
     L = sl.cholesky(V, lower=True, check_finite=False)
     T = int3c(mol).reshape(mol.naux, -1)
-    B = sl.solve_triangular(L, T, lower=True, overwrite_b=True, check_finite=False)
-    return np.ascontiguousarray(B.reshape(mol.naux, mol.nao, mol.nao))
+    # B^T = T^T L^{-T}: a right-side solve on the Fortran-order view of T (no copy)
+    Bt = dtrsm(1.0, L, T.T, side=1, lower=1, trans_a=1, overwrite_b=1)
+    B = np.ascontiguousarray(Bt.T).reshape(mol.naux, mol.nao, mol.nao)
+    # every B_P is symmetric in (mu, nu); make it so bit for bit whatever the BLAS did
+    for P in range(mol.naux):
+        B[P] = 0.5 * (B[P] + B[P].T)
+    return B
 
 
 def orbitals(nao: int, nocc: int, seed: int) -> np.ndarray:
@@ -151,7 +157,9 @@ def orbitals(nao: int, nocc: int, seed: int) -> np.ndarray:
 
 
 def density(C: np.ndarray) -> np.ndarray:
-    return 2.0 * C @ C.T
+    """D = 2 C C^T, symmetric bit for bit."""
+    D = 2.0 * C @ C.T
+    return 0.5 * (D + D.T)
 
 
 def perturbed_orbitals(C_star: np.ndarray, k: int, seed: int, base: float = 0.1) -> tuple[np.ndarray, float]:
@@ -211,6 +219,11 @@ SMALL = Workload("df-20atom-nao100-naux300-nocc20", 20, 20, 1000 * 0 + 0)
 MEDIUM = Workload("df-120atom-nao600-naux1800-nocc120", 120, 120, 1000 * 1 + 0)
 # One molecule of 240 atoms (nao 1200, naux 3600, nocc 250): adaptive sequence.
 LARGE = Workload("df-240atom-nao1200-naux3600-nocc250", 240, 250, 1000 * 2 + 0)
+
+
+# 60 atoms with the 120-atom molecule's occupied count: the same tile shapes in a
+# few GB of device memory (used for counter captures).
+PROFILE = Workload("df-60atom-nao300-naux900-nocc120", 60, 120, 1000 * 9 + 0)
 
 
 def batch_workloads(n_mol: int = 48, seed: int = 3000) -> list[Workload]:

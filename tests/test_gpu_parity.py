@@ -1,0 +1,287 @@
+"""GPU parity of libdf against the CPU oracle, through the C ABI.
+
+Integer work (digits, exponents, slice-pair products) must be bit-exact.
+FP64 results must be bit-exact where the fixed-point recombination is exact
+(truncation T = 0), and otherwise within the bound of the dropped bits; the
+J/K builds must meet the benchmark spec's tolerances max|dK| <= 1e-10 max|K| and
+|dE| <= 1e-9 Eh at the full slice count.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import df_oracle as O
+from paper_2601_08077_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def df():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_08077_gb300 import build, df as dfmod
+    build.build_all()
+    return dfmod
+
+
+@pytest.fixture(scope="module")
+def small():
+    mol, B, C, D = inputs.make_inputs(inputs.SMALL)
+    return B, C, D
+
+
+@pytest.fixture(scope="module")
+def medium():
+    mol, B, C, D = inputs.make_inputs(inputs.MEDIUM)
+    return B, C, D
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def spread(rng, m, n, spread=20):
+    return rng.standard_normal((m, n)) * np.exp2(rng.integers(-spread, 1, size=(m, n)))
+
+
+def shift_T(s, k):
+    """Truncation of the int64 fixed-point sum (same rule as the library)."""
+    bound = sum((g + 1) * k * 16384 * 2 ** (8 * (s - 1 - g)) for g in range(s))
+    bits = 0
+    while 2 ** bits < bound:
+        bits += 1
+    return max(0, bits - 61)
+
+
+def n_chunks(s, ktiles):
+    return sum(-(-((g + 1) * ktiles) // 16) for g in range(s))
+
+
+# --- split ------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(1, 1), (37, 53), (300, 1100), (129, 64)])
+def test_split_bitexact(df, shape):
+    rng = np.random.default_rng(sum(shape))
+    A = spread(rng, *shape)
+    A[0, : shape[1] // 2] = 0.0
+    if shape[0] > 5:
+        A[5] = 0.0
+        A[3, 0] = 127 / 128 * 2.0 ** 7          # exactly on the headroom boundary
+        A[4, -1] = -(2.0 ** -1070)              # subnormal
+    e_ref, d_ref = O.split_rows(A, 8)
+    e, d = df.split_int8(cuda(A), 8)
+    assert np.array_equal(e.cpu().numpy(), e_ref.astype(np.int32))
+    assert np.array_equal(d.cpu().numpy(), d_ref)
+
+
+# --- slice-pair products -------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5, 8])
+def test_slice_products_bitexact(df, s):
+    rng = np.random.default_rng(100 + s)
+    M, N, K = 300, 200, 1100      # 3 x 2 tiles with ragged edges; K > 1024 forces several chunks
+    A = spread(rng, M, K, 10)
+    B = spread(rng, N, K, 10)
+    S, ea, eb = df.slice_products(cuda(A), cuda(B), s)
+    ea_ref, Ad = O.split_rows(A, s)
+    eb_ref, Bd = O.split_rows(B, s)
+    S_ref = O.slice_products(Ad, Bd, s)
+    assert np.array_equal(ea.cpu().numpy(), ea_ref.astype(np.int32))
+    assert np.array_equal(eb.cpu().numpy(), eb_ref.astype(np.int32))
+    assert np.array_equal(S.cpu().numpy(), S_ref)
+
+
+def test_slice_products_at_the_exactness_limit(df):
+    """Same-sign rows with near-full digits drive every 1024-product chunk to ~2^24."""
+    K = 4096
+    A = np.empty((130, K))
+    A[:] = 0.9999999 * 0.992
+    A[1::2] = -A[1::2]
+    A[7] = 0.9921875 - 2.0 ** -40   # 127/128 - tiny: top digit 127, low digits near -128
+    B = np.empty((140, K))
+    B[:] = -(0.9921875 - 2.0 ** -45)
+    s = 8
+    S, _, _ = df.slice_products(cuda(A), cuda(B), s)
+    ea, Ad = O.split_rows(A, s)
+    eb, Bd = O.split_rows(B, s)
+    S_ref = O.slice_products(Ad, Bd, s)
+    per_chunk = np.abs(Ad[0].astype(np.int64)).max() * np.abs(Bd[0].astype(np.int64)).max() * 1024
+    assert per_chunk > 2 ** 23          # the test really reaches the FP32 exactness limit
+    assert np.array_equal(S.cpu().numpy(), S_ref)
+
+
+# --- emulated product ----------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [1, 3, 4, 5, 6, 8])
+def test_emulated_gemm_vs_oracle(df, s):
+    rng = np.random.default_rng(200 + s)
+    M, N, K = 150, 260, 700
+    A = spread(rng, M, K, 14)
+    B = spread(rng, N, K, 14)
+    got = df.emulated_gemm(cuda(A), cuda(B), s).cpu().numpy()
+    ref = O.emulated_matmul(A, B.T, s)
+    ktiles = -(-K // 64)
+    T = shift_T(s, ktiles * 64)
+    if T == 0:
+        assert np.array_equal(got, ref)
+    else:
+        ea, eb = O.row_exponents(A), O.row_exponents(B)
+        unit = np.ldexp(1.0, (ea[:, None] + eb[None, :] - 14 - 8 * (s - 1) + T).astype(np.int64))
+        bound = unit * (0.5 * n_chunks(s, ktiles) + 1) + 2 * np.spacing(np.abs(ref))
+        assert np.all(np.abs(got - ref) <= bound)
+
+
+# --- the DF builds --------------------------------------------------------------------------
+
+def _ctx(df, B, nocc):
+    naux, nao, _ = B.shape
+    ctx = df.Context(nao, naux, nocc)
+    Bt = cuda(B)
+    ctx.setup(Bt)
+    return ctx, Bt
+
+
+@pytest.mark.parametrize("s", [3, 4, 5])
+def test_exchange_small_bitexact_vs_oracle_emulation(df, small, s):
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    K, st = ctx.build_K(cuda(C), s)
+    ref = O.emulated_exchange(B, C, s)
+    assert np.array_equal(K.cpu().numpy(), ref)
+    assert st.nblk == 3 and list(st.slices[:3]) == [s] * 3
+
+
+@pytest.mark.parametrize("s", [6, 7, 8])
+def test_exchange_small_high_slices(df, small, s):
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    K = ctx.build_K(cuda(C), s)[0].cpu().numpy()
+    Kem = O.emulated_exchange(B, C, s)
+    Kfp = O.exchange(B, C)
+    scale = np.max(np.abs(Kfp))
+    assert np.max(np.abs(K - Kem)) <= 1e-14 * scale
+    assert np.max(np.abs(K - Kfp)) <= 1e-10 * scale
+    assert np.array_equal(K, K.T)
+
+
+def fp64_exchange_bound(B, C):
+    """Two FP64 builds of K in different orders differ by at most twice the
+    standard dot-product bound: gamma_n sum|terms| for X (n = nao) propagated
+    into K, plus gamma_n sum|X||X| for K itself (n = naux nocc)."""
+    u = 2.0 ** -53
+    naux, nao, _ = B.shape
+    nocc = C.shape[1]
+    Xa = np.abs(B) @ np.abs(C)                      # bound on sum |B||C| per X element
+    X = np.abs(B @ C)
+    Xa_t = Xa.transpose(1, 0, 2).reshape(nao, -1)
+    X_t = X.transpose(1, 0, 2).reshape(nao, -1)
+    g1, g2 = 1.01 * nao * u, 1.01 * naux * nocc * u
+    return 2 * (g1 * (Xa_t @ X_t.T + X_t @ Xa_t.T) + g2 * (X_t @ X_t.T)) + 1e-300
+
+
+def test_exchange_native_fp64(df, small):
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    K, st = ctx.build_K(cuda(C), 0)
+    Kfp = O.exchange(B, C)
+    assert st.fallback == 1
+    assert np.all(np.abs(K.cpu().numpy() - Kfp) <= fp64_exchange_bound(B, C))
+
+
+def test_exchange_per_block_slices(df, small):
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    sl = [5, 3, 4]
+    K, st = ctx.build_K_blocks(cuda(C), sl)
+    assert list(st.slices[:3]) == sl
+    assert np.array_equal(K.cpu().numpy(), O.emulated_exchange(B, C, sl))
+
+
+def test_coulomb_and_energies(df, small):
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    Dg = cuda(D)
+    J, rho = ctx.build_J(Dg)
+    K, _ = ctx.build_K(cuda(C), 8)
+    r_ref = O.rho(B, D)
+    J_ref = O.coulomb(B, r_ref)
+    # FP64 sums in another order: |error| <= n u sum|terms| (n = nao^2 and naux terms)
+    tol_r = 2 * B.shape[1] ** 2 * 2.0 ** -53 * np.abs(B).reshape(B.shape[0], -1) @ np.abs(D).ravel()
+    assert np.all(np.abs(rho.cpu().numpy() - r_ref) <= tol_r + 1e-300)
+    tol_J = 2 * B.shape[0] * 2.0 ** -53 * np.einsum("pmn,p->mn", np.abs(B), np.abs(r_ref)) + 1e-300
+    assert np.all(np.abs(J.cpu().numpy() - J_ref) <= tol_J + np.einsum("pmn,p->mn", np.abs(B), tol_r))
+    EJ, EJ2, EK = ctx.energy(Dg, J, K, rho)
+    EJ_ref, EK_ref = O.energies(D, J_ref, O.exchange(B, C))
+    assert abs(EJ - EJ_ref) <= 1e-9 and abs(EJ2 - EJ_ref) <= 1e-9 and abs(EK - EK_ref) <= 1e-9
+    assert abs(EJ - EJ2) <= 1e-12 * abs(EJ)
+
+
+def test_adaptive_controller_matches_rule(df, small):
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    E = [-100.0, -100.5, -100.5001, -100.4, -100.50010001, -100.500100010001, -100.500100010001]
+    levels = O.level_schedule(E)
+    ctx.adaptive_reset()
+    got = [4]
+    for e in E:
+        lv, ns = ctx.adaptive_next(e)
+        got.append(lv)
+        assert ns == O.slices_for_level(lv)
+    assert got == levels
+    for x in [1.0, 2e-6, 1.9999e-6, 5e-9, 4.9e-9, 2e-11, 1.9e-11, 7e-14, 6.9e-14, 0.0]:
+        assert df.level_for(x) == O.level_for(x)
+
+
+def test_adaptive_fp64_fallback_level(df, small):
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    ctx.adaptive_reset(fp64_from_level=3)       # e.g. hardware where FP64 wins below level 4
+    ctx.adaptive_next(-100.0)
+    ctx.adaptive_next(-100.0000001)             # dE_rel ~ 1e-9 -> level 2
+    lv, ns = ctx.adaptive_next(-100.00000011)
+    assert lv <= 3 and ns == 0
+
+
+def test_errors_are_reported(df, small):
+    B, C, D = small
+    ctx = df.Context(B.shape[1], B.shape[0], C.shape[1])
+    with pytest.raises(df.DFError) as e:
+        ctx.build_K(cuda(C), 3)                  # before setup
+    assert e.value.status == -7
+    ctx.setup(cuda(B))
+    with pytest.raises(df.DFError) as e:
+        ctx.build_K(cuda(C), 9)
+    assert e.value.status == -1
+    ctx.sync_status()
+
+
+# --- the 120-atom molecule: the fixed-slice sweep ---------------------------------------------
+
+def test_medium_sweep_against_fp64_oracle(df, medium):
+    B, C, D = medium
+    ctx, _ = _ctx(df, B, C.shape[1])
+    Kfp = O.exchange(B, C)
+    scale = np.max(np.abs(Kfp))
+    Cg = cuda(C)
+    errs = {}
+    for s in range(3, 9):
+        K = ctx.build_K(Cg, s)[0].cpu().numpy()
+        errs[s] = np.max(np.abs(K - Kfp)) / scale
+        assert np.array_equal(K, K.T)
+    assert errs[3] > errs[4] > errs[5] > errs[6]
+    assert errs[3] < 1e-5
+    assert errs[5] <= 1e-10 and errs[8] <= 1e-10
+    Kn = ctx.build_K(Cg, 0)[0].cpu().numpy()
+    assert np.all(np.abs(Kn - Kfp) <= fp64_exchange_bound(B, C))
+    Dg = cuda(D)
+    J, rho = ctx.build_J(Dg)
+    r_ref = O.rho(B, D)
+    J_ref = O.coulomb(B, r_ref)
+    assert np.max(np.abs(J.cpu().numpy() - J_ref)) <= 1e-12 * np.max(np.abs(J_ref))
+    K8 = ctx.build_K(Cg, 8)[0]
+    EJ, EJ2, EK = ctx.energy(Dg, J, K8, rho)
+    EJ_ref, EK_ref = O.energies(D, J_ref, Kfp)
+    assert abs(EJ - EJ_ref) <= 1e-9 and abs(EK - EK_ref) <= 1e-9
