@@ -44,7 +44,8 @@ typedef enum {
   DF_ERR_NOT_PD = -4,   /* metric not positive definite */
   DF_ERR_TIMEOUT = -5,  /* a bounded device-side wait ran out */
   DF_ERR_TOL = -6,      /* a result missed its tolerance after recompute */
-  DF_ERR_STATE = -7     /* call out of order (e.g. build before setup) */
+  DF_ERR_STATE = -7,    /* call out of order (e.g. build before setup) */
+  DF_ERR_SCRATCH = -8   /* problem too large for df_emulated_gemm_static's fixed scratch */
 } df_status;
 
 typedef struct df_ctx df_ctx;
@@ -117,6 +118,19 @@ df_status df_slice_products(const double *A_dev, const double *B_dev, int M, int
  * device, row-major) with nslices INT8 slices per operand (Section 3.2). */
 df_status df_emulated_gemm(const double *A_dev, const double *B_dev, int M, int N, int K, int nslices,
                            double *out_dev, void *stream);
+
+/* Same result as df_emulated_gemm, but allocates nothing (the paper has no
+ * counterpart: this serves callers that cannot let a library allocate, such
+ * as a framework whose memory pool already holds nearly all device memory, or
+ * a latency-critical loop that cannot take the synchronisation of
+ * cudaMalloc/cudaFree).  Scratch comes from one static 32 MiB device array per
+ * GPU; sizes needing more than that (digit planes 2 * nslices * (M + N) *
+ * round_up(K, 8) bytes plus exponents) return DF_ERR_SCRATCH.  The first call
+ * on a device looks up the array's device address with that device current:
+ * make it before any stream capture.  Calls share the array, so calls whose
+ * GPU work overlaps race.  Synchronises `stream`. */
+df_status df_emulated_gemm_static(const double *A_dev, const double *B_dev, int M, int N, int K, int nslices,
+                                  double *out_dev, void *stream);
 
 /* Table 1 (Section 3.2): the emulation level for the next iteration given the
  * relative energy change (>= lower bound of the row); level 0 = FP64. */

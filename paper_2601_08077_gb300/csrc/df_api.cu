@@ -262,6 +262,7 @@ const char *df_strerror(df_status s) {
     case DF_ERR_TIMEOUT: return "bounded device wait ran out";
     case DF_ERR_TOL: return "result missed its tolerance";
     case DF_ERR_STATE: return "call out of order";
+    case DF_ERR_SCRATCH: return "problem exceeds the 32 MiB static scratch of df_emulated_gemm_static";
   }
   return "unknown status";
 }
