@@ -29,7 +29,8 @@ struct df_ctx {
   double *X = nullptr;
   uint16_t *Xd = nullptr;
   int *eX = nullptr;
-  double *Kp = nullptr;
+  long long *Rp = nullptr;  // int64 partials of the second GEMM [nblk][nsplit][nao][nao]
+  int nsplit = 1;
   double *rho = nullptr;
   double *epart = nullptr;
   double *E = nullptr;
@@ -216,7 +217,8 @@ df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, 
   q2.layout = df::kLayoutKPart;
   q2.mode = df::kModeKPart;
   q2.nt_m = q2.nt_n = (nao + df::kTile - 1) / df::kTile;
-  q2.nunits = q2.nt_m * (q2.nt_m + 1) / 2 * c->nblk;
+  q2.nsplit = c->nsplit;
+  q2.nunits = q2.nt_m * (q2.nt_m + 1) / 2 * c->nblk * c->nsplit;
   q2.m_valid = q2.n_valid = nao;
   q2.nao = nao;
   q2.nocc = nocc;
@@ -226,7 +228,7 @@ df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, 
   for (int q = 0; q <= 8; ++q) q2.shiftT[q] = df::fixed_point_shift(q, kb_ld);
   q2.ea = c->eX;
   q2.eb = c->eX;
-  q2.out = c->Kp;
+  q2.raw = c->Rp;
   q2.out_ld = nao;
   q2.out_blk = (long long)nao * nao;
   q2.status = c->status;
@@ -237,7 +239,9 @@ df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, 
   // 5. K = sum_b K_b
   {
     PhaseTimer t(c, DF_PHASE_REDUCE, st);
-    DF_TRY(c, df::launch_kpart_reduce(c->Kp, nao, c->nblk, K, st));
+    df::ShiftTable tt;
+    for (int q = 0; q <= 8; ++q) tt.v[q] = q2.shiftT[q];
+    DF_TRY(c, df::launch_kpart_reduce(c->Rp, c->eX, c->sblk, tt, nao, c->nblk, c->nsplit, K, st));
   }
   if (stats) {
     stats->nblk = c->nblk;
@@ -303,7 +307,17 @@ df_status df_create(df_ctx **out, int nao, int naux, int nocc_max, int s_max) {
   if (e == cudaSuccess) e = alloc(c, &c->X, (size_t)rowsB * nocc_max);
   if (e == cudaSuccess) e = alloc(c, &c->Xd, (size_t)s_max * c->nblk * nao * c->kb_ld_max);
   if (e == cudaSuccess) e = alloc(c, &c->eX, (size_t)c->nblk * nao);
-  if (e == cudaSuccess) e = alloc(c, &c->Kp, (size_t)c->nblk * nao * nao);
+  {
+    // split the K range of each block so the second GEMM has >= 3 work units per SM
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nt = (nao + df::kTile - 1) / df::kTile;
+    const long long units = (long long)nt * (nt + 1) / 2 * c->nblk;
+    long long ns = (3LL * nsm + units - 1) / units;
+    c->nsplit = (int)(ns < 1 ? 1 : (ns > 8 ? 8 : ns));
+  }
+  if (e == cudaSuccess) e = alloc(c, &c->Rp, (size_t)c->nblk * c->nsplit * nao * nao);
   if (e == cudaSuccess) e = alloc(c, &c->rho, (size_t)naux);
   if (e == cudaSuccess) e = alloc(c, &c->epart, (size_t)3 * 296);
   if (e == cudaSuccess) e = alloc(c, &c->E, (size_t)4);
@@ -332,7 +346,7 @@ void df_destroy(df_ctx *c) {
   cudaFree(c->X);
   cudaFree(c->Xd);
   cudaFree(c->eX);
-  cudaFree(c->Kp);
+  cudaFree(c->Rp);
   cudaFree(c->rho);
   cudaFree(c->epart);
   cudaFree(c->E);

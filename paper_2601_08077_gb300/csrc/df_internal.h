@@ -19,7 +19,8 @@ constexpr int kMaxChunk = 1024;  // products per exact FP32 accumulation chunk
 // Epilogue modes of the slice GEMM.
 enum SgMode : int {
   kModeX = 0,       // first exchange GEMM: X[n*ld + m] (transposed tile of X^T = C^T B^T)
-  kModeKPart = 1,   // second exchange GEMM: per-block partial K, out[b*blk + n*ld + m]
+  kModeKPart = 1,   // second exchange GEMM: int64 fixed-point partial per (block, K split),
+                    // raw[part*blk + n*ld + m] (the reduce scales and sums them)
   kModeRaw = 2,     // exact S_g per group: raw[(g*n_valid + n)*m_valid + m]
   kModeGemm = 3,    // generic emulated product: out[m*ld + n]
 };
@@ -39,6 +40,7 @@ struct SgParams {
   int ktiles;               // K tiles (64 wide) for kLayoutGrid / kLayoutX
   int s_fixed;              // slice count for kLayoutGrid
   int nao, nocc, nblk, naux;
+  int nsplit;               // K splits per block (kLayoutKPart)
   const int *s_blk;         // per-block slice counts (kLayoutX, kLayoutKPart)
   int shiftT[9];            // truncation T of the fixed-point sum, indexed by s (0..8)
   const int *ea;            // A-side row exponents
@@ -62,7 +64,11 @@ cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int ns
                                    uint16_t *digits, long long dld, long long plane_stride, cudaStream_t st);
 cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, int nslices, int *eX,
                                  uint16_t *Xd, long long kb_ld, int nblk, cudaStream_t st);
-cudaError_t launch_kpart_reduce(const double *Kp, int nao, int nblk, double *K, cudaStream_t st);
+struct ShiftTable {
+  int v[9];
+};
+cudaError_t launch_kpart_reduce(const long long *Rp, const int *eX, const int *s_blk, ShiftTable T, int nao,
+                                int nblk, int nsplit, double *K, cudaStream_t st);
 
 // Encode a 3D bf16 tensor map {k, rows, planes} with a 64 x 128 x 1 box, 128B swizzle.
 bool make_tmap_bf16(CUtensorMap *map, const void *base, long long k, long long rows, long long planes,

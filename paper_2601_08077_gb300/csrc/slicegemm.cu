@@ -15,16 +15,20 @@
 // two digits is at most 2^14 in magnitude, so an accumulation of at most 1024
 // products stays within 2^24 and is exact in FP32; the MMA warp therefore
 // closes an accumulator "chunk" every 1024 products (16 pipeline stages) and
-// the epilogue warps fold it exactly into an int64 running sum that also
-// lives in TMEM.  Two FP32 accumulator buffers (columns 0-255) let the tensor
-// core fill one while the epilogue drains the other; the int64 sums use
-// columns 256-511 (two 32-bit columns per output column).
+// the epilogue warps add it exactly into an int32 sum of the group held in
+// registers (one convert and one integer add per element per chunk).  At the
+// end of a group (or every 64 chunks, before the int32 sum could overflow)
+// the group sum is folded, shifted by its group's weight, into an int64
+// fixed-point total kept in TMEM.  TMEM columns 0-255 hold two FP32
+// accumulator buffers (the tensor core fills one while the epilogue drains
+// the other), columns 256-511 the int64 totals (two 32-bit columns each).
 //
-// Warp roles (192 threads, one CTA per SM, persistent over work units):
+// Warp roles (320 threads, one CTA per SM, persistent over work units):
 //   warp 0      TMA producer: 128x64 BF16 boxes of A_t and B_u, 128B swizzle,
 //               into a 6-stage ring (32 KB per stage) guarded by mbarriers;
 //   warp 1      TMEM allocation and the single-thread tcgen05.mma issuer;
-//   warps 2..5  epilogue; warp w reads TMEM lanes 32*(w%4)..+31 (tile rows).
+//   warps 2..9  epilogue; warp w reads TMEM lanes 32*(w%4)..+31 (tile rows)
+//               and columns 64*((w-2)/4)..+63.
 //
 // Every mbarrier wait is bounded (4 s of wall clock); a wait that runs out
 // sets a shared abort flag and bit 1 of the device status word, every role
@@ -41,9 +45,12 @@ namespace {
 constexpr int kStages = 6;
 constexpr int kTileBytes = kTile * kKTile * 2;  // 16 KB of BF16
 constexpr int kStageBytes = 2 * kTileBytes;     // A tile + B tile
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kAccBufs = 2;
+constexpr uint32_t kRCol = 256;     // int64 totals: lo words at +0..63, hi words at +64..127 per half
+constexpr int kFoldChunks = 64;     // 64 chunks x 2^24 < 2^31: int32 group sums never overflow
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kRCol = 256;
 constexpr int kChunkStages = kMaxChunk / kKTile;  // 16 stages = 1024 products
 constexpr uint64_t kTimeoutNs = 4000000000ull;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*alignment slack*/;
@@ -55,7 +62,7 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTi
                             ((uint32_t)(kTile >> 4) << 24);
 
 struct Unit {
-  int m0, n0, az0, azs, bz0, bzs, ktiles, s, blk;
+  int m0, n0, az0, azs, bz0, bzs, kt0, ktiles, s, blk, part;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -172,9 +179,12 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
   Unit w;
   if (p.layout == kLayoutKPart) {
+    // u -> (block b, K split sp, upper tile pair); block-major for L2 reuse
     const int npairs = p.nt_m * (p.nt_m + 1) / 2;
     const int pr = u % npairs;
-    const int b = u / npairs;
+    const int bs = u / npairs;
+    const int b = bs / p.nsplit;
+    const int sp = bs - b * p.nsplit;
     int i = 0, rem = pr;
     while (rem >= p.nt_m - i) {
       rem -= p.nt_m - i;
@@ -187,9 +197,12 @@ __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
     w.bz0 = b;
     w.bzs = p.nblk;
     const int nP = min(kBlock, p.naux - b * kBlock);
-    w.ktiles = (nP * p.nocc + kKTile - 1) / kKTile;
+    const int kt_b = (nP * p.nocc + kKTile - 1) / kKTile;
+    w.kt0 = (int)((long long)kt_b * sp / p.nsplit);
+    w.ktiles = (int)((long long)kt_b * (sp + 1) / p.nsplit) - w.kt0;
     w.s = p.s_blk[b];
     w.blk = b;
+    w.part = bs;
   } else {
     const int mt = u % p.nt_m;
     const int nt = u / p.nt_m;
@@ -199,6 +212,8 @@ __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
     w.azs = 1;
     w.bz0 = 0;
     w.bzs = 1;
+    w.kt0 = 0;
+    w.part = 0;
     w.ktiles = p.ktiles;
     if (p.layout == kLayoutX) {
       w.blk = (int)((long long)w.n0 / ((long long)kBlock * p.nao));
@@ -211,31 +226,38 @@ __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
   return w;
 }
 
-// Epilogue store of 16 consecutive output columns n0c..n0c+15 of row m.
-__device__ __forceinline__ void store16(const SgParams &p, const Unit &w, int m, int n0c, int g,
-                                        const uint32_t (&lo)[16], const uint32_t (&hi)[16], int kexp_base,
-                                        int ea_m) {
+// Epilogue store of 16 consecutive output columns n0c..n0c+15 of row m from
+// the int64 totals (lo/hi words).
+template <int kMode>
+__device__ __forceinline__ void store16(const SgParams &p, const Unit &w, int m, int n0c, const uint32_t (&lo)[16],
+                                        const uint32_t (&hi)[16], int kexp_base, int ea_m) {
   if (m >= p.m_valid) return;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const int n = n0c + j;
-    if (n >= p.n_valid) break;
+    if (n >= p.n_valid) continue;
     const long long R = (long long)(((uint64_t)hi[j] << 32) | (uint64_t)lo[j]);
-    if (p.mode == kModeRaw) {
-      p.raw[((long long)g * p.n_valid + n) * p.m_valid + m] = R;
-    } else if (p.mode == kModeX) {
-      const double v = ldexp_i64(R, kexp_base + ea_m + p.eb[n]);
-      p.out[(long long)n * p.out_ld + m] = v;
-    } else if (p.mode == kModeKPart) {
-      const double v = ldexp_i64(R, kexp_base + ea_m + p.eb[(long long)w.blk * p.nao + n]);
-      p.out[(long long)w.blk * p.out_blk + (long long)n * p.out_ld + m] = v;
+    if (kMode == kModeX) {
+      p.out[(long long)n * p.out_ld + m] = ldexp_i64(R, kexp_base + ea_m + p.eb[n]);
+    } else if (kMode == kModeKPart) {
+      p.raw[(long long)w.part * p.out_blk + (long long)n * p.out_ld + m] = R;
     } else {
-      const double v = ldexp_i64(R, kexp_base + ea_m + p.eb[n]);
-      p.out[(long long)m * p.out_ld + n] = v;
+      p.out[(long long)m * p.out_ld + n] = ldexp_i64(R, kexp_base + ea_m + p.eb[n]);
     }
   }
 }
 
+// Raw mode: the exact group sum S_g of 64 consecutive columns.
+__device__ __forceinline__ void store_raw(const SgParams &p, int m, int n0c, int g, const int (&S)[64]) {
+  if (m >= p.m_valid) return;
+#pragma unroll
+  for (int j = 0; j < 64; ++j) {
+    const int n = n0c + j;
+    if (n < p.n_valid) p.raw[((long long)g * p.n_valid + n) * p.m_valid + m] = (long long)S[j];
+  }
+}
+
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
                       const SgParams p) {
@@ -244,8 +266,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
   uint64_t *empty = full + kStages;
   uint64_t *acc_full = empty + kStages;
-  uint64_t *acc_empty = acc_full + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  uint64_t *acc_empty = acc_full + kAccBufs;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + kAccBufs);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -256,9 +278,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kAccBufs; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 4);
+      mbar_init(&acc_empty[i], kEpiWarps);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -293,8 +315,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint8_t *sa = smem + stage * kStageBytes;
               uint8_t *sb = sa + kTileBytes;
               mbar_expect_tx(&full[stage], kStageBytes);
-              tma_load_3d(sa, &tmap_a, &full[stage], kt * kKTile, w.m0, w.az0 + t * w.azs);
-              tma_load_3d(sb, &tmap_b, &full[stage], kt * kKTile, w.n0, w.bz0 + (g - t) * w.bzs);
+              tma_load_3d(sa, &tmap_a, &full[stage], (w.kt0 + kt) * kKTile, w.m0, w.az0 + t * w.azs);
+              tma_load_3d(sb, &tmap_b, &full[stage], (w.kt0 + kt) * kKTile, w.n0, w.bz0 + (g - t) * w.bzs);
               ++it;
             }
           }
@@ -319,9 +341,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kt = 0; kt < w.ktiles; ++kt) {
             const uint32_t stage = it % kStages;
             const uint32_t ph = (it / kStages) & 1;
-            const uint32_t buf = qc & 1;
+            const uint32_t buf = qc % kAccBufs;
             if (chunk_pos == 0) {
-              if (!wait_bounded(&acc_empty[buf], ((qc >> 1) & 1) ^ 1, abort_flag, p.status)) {
+              if (!wait_bounded(&acc_empty[buf], ((qc / kAccBufs) & 1) ^ 1, abort_flag, p.status)) {
                 ok = false;
                 break;
               }
@@ -358,82 +380,109 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (!ok && lane == 0) {
       // wait for the MMAs already issued before the TMEM is released
-      uint64_t *done = &acc_full[qc & 1];
+      uint64_t *done = &acc_full[qc % kAccBufs];
       umma_commit(done);
-      wait_bounded(done, (qc >> 1) & 1, abort_flag, p.status, false);
+      wait_bounded(done, (qc / kAccBufs) & 1, abort_flag, p.status, false);
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
     const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
-    const uint32_t taddr_lane = tmem_base + ((uint32_t)(quad * 32) << 16);
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+    const uint32_t acc_addr = lane_base + (uint32_t)(half * 64);
+    const uint32_t r_addr = lane_base + kRCol + (uint32_t)(half * 128);
+    int S[64];
     uint32_t qc = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
       const Unit w = decode_unit(p, u);
       const int s = w.s;
-      const int T = p.mode == kModeRaw ? 0 : p.shiftT[s];
+      const int T = kMode == kModeRaw ? 0 : p.shiftT[s];
       const int m = w.m0 + row;
+      const int n_base = w.n0 + half * 64;
       int ea_m = 0;
-      if (p.mode != kModeRaw && m < p.m_valid)
-        ea_m = p.mode == kModeKPart ? p.ea[(long long)w.blk * p.nao + m] : p.ea[m];
+      if ((kMode == kModeX || kMode == kModeGemm) && m < p.m_valid) ea_m = p.ea[m];
       const int kexp_base = -14 - 8 * (s - 1) + T;
-      bool first = true;
+      bool r_zero = true;  // the int64 totals of this unit start at zero
       for (int g = 0; g < s && ok; ++g) {
         const int nst = (g + 1) * w.ktiles;
         const int nch = (nst + kChunkStages - 1) / kChunkStages;
-        const int sh = p.mode == kModeRaw ? 0 : 8 * (s - 1 - g) - T;
+        const int sh = 8 * (s - 1 - g) - T;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) S[j] = 0;
         for (int c = 0; c < nch; ++c) {
-          const uint32_t buf = qc & 1;
-          if (!wait_bounded(&acc_full[buf], (qc >> 1) & 1, abort_flag, p.status)) {
+          const uint32_t buf = qc % kAccBufs;
+          if (!wait_bounded(&acc_full[buf], (qc / kAccBufs) & 1, abort_flag, p.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-#pragma unroll 1
-          for (int cb = 0; cb < kTile / 16; ++cb) {
-            uint32_t a[16], lo[16], hi[16];
-            tmem_ld16(taddr_lane + buf * kTile + cb * 16, a);
-            if (!first) {
-              tmem_ld16(taddr_lane + kRCol + cb * 32, lo);
-              tmem_ld16(taddr_lane + kRCol + cb * 32 + 16, hi);
-            }
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            uint32_t a0[16], a1[16];
+            tmem_ld16(acc_addr + buf * kTile + hh * 32, a0);
+            tmem_ld16(acc_addr + buf * kTile + hh * 32 + 16, a1);
             tmem_wait_ld();
+            if (hh == 1) {
+              // the whole buffer is in registers: hand it back to the MMA warp
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const long long v = (long long)__float2int_rz(__uint_as_float(a[j]));
-              long long add;
-              if (sh >= 0)
-                add = v << sh;
-              else
-                add = (v + (1ll << (-sh - 1))) >> (-sh);
-              long long R = first ? 0ll : (long long)(((uint64_t)hi[j] << 32) | (uint64_t)lo[j]);
-              R += add;
-              lo[j] = (uint32_t)((uint64_t)R & 0xFFFFFFFFull);
-              hi[j] = (uint32_t)((uint64_t)R >> 32);
+              S[hh * 32 + j] += __float2int_rz(__uint_as_float(a0[j]));
+              S[hh * 32 + 16 + j] += __float2int_rz(__uint_as_float(a1[j]));
             }
-            tmem_st16(taddr_lane + kRCol + cb * 32, lo);
-            tmem_st16(taddr_lane + kRCol + cb * 32 + 16, hi);
           }
-          tmem_wait_st();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acc_empty[buf]);
           ++qc;
-          first = false;
-          const bool last_of_group = (c == nch - 1);
-          if (last_of_group && (p.mode == kModeRaw || g == s - 1)) {
-            // write the finished tile (per group in raw mode)
-#pragma unroll 1
-            for (int cb = 0; cb < kTile / 16; ++cb) {
+          const bool fold = (c == nch - 1) || ((c + 1) % kFoldChunks == 0);
+          if (kMode != kModeRaw && fold) {
+            // R += S << sh (or rounded >> -sh), 16 columns at a time
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
               uint32_t lo[16], hi[16];
-              tmem_ld16(taddr_lane + kRCol + cb * 32, lo);
-              tmem_ld16(taddr_lane + kRCol + cb * 32 + 16, hi);
-              tmem_wait_ld();
-              store16(p, w, m, w.n0 + cb * 16, g, lo, hi, kexp_base, ea_m);
+              if (!r_zero) {
+                tmem_ld16(r_addr + q * 16, lo);
+                tmem_ld16(r_addr + 64 + q * 16, hi);
+                tmem_wait_ld();
+              }
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const long long v = (long long)S[q * 16 + j];
+                const long long add = sh >= 0 ? (v << sh) : ((v + (1ll << (-sh - 1))) >> (-sh));
+                const long long R =
+                    (r_zero ? 0ll : (long long)(((uint64_t)hi[j] << 32) | (uint64_t)lo[j])) + add;
+                lo[j] = (uint32_t)((uint64_t)R & 0xFFFFFFFFull);
+                hi[j] = (uint32_t)((uint64_t)R >> 32);
+                S[q * 16 + j] = 0;
+              }
+              tmem_st16(r_addr + q * 16, lo);
+              tmem_st16(r_addr + 64 + q * 16, hi);
             }
-            if (p.mode == kModeRaw) first = true;
+            tmem_wait_st();
+            r_zero = false;
+          }
+        }
+        if (!ok) break;
+        if (kMode == kModeRaw) {
+          store_raw(p, m, n_base, g, S);
+        } else if (g == s - 1) {
+          // the unit is complete: scale and store the int64 totals
+#pragma unroll 1
+          for (int q = 0; q < 4; ++q) {
+            uint32_t lo[16], hi[16];
+            if (!r_zero) {
+              tmem_ld16(r_addr + q * 16, lo);
+              tmem_ld16(r_addr + 64 + q * 16, hi);
+              tmem_wait_ld();
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) lo[j] = hi[j] = 0u;
+            }
+            store16<kMode>(p, w, m, n_base + q * 16, lo, hi, kexp_base, ea_m);
           }
         }
       }
@@ -508,16 +557,28 @@ int slice_gemm_grid(int nunits) {
   return nunits < nsm ? nunits : nsm;
 }
 
-cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
-  if (p.nunits <= 0) return cudaSuccess;
+template <int kMode>
+cudaError_t launch_mode(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(slice_gemm_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  slice_gemm_kernel<<<slice_gemm_grid(p.nunits), kThreads, kSmemBytes, st>>>(ta, tb, p);
+  slice_gemm_kernel<kMode><<<slice_gemm_grid(p.nunits), kThreads, kSmemBytes, st>>>(ta, tb, p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
+  if (p.nunits <= 0) return cudaSuccess;
+  switch (p.mode) {
+    case kModeX: return launch_mode<kModeX>(p, ta, tb, st);
+    case kModeKPart: return launch_mode<kModeKPart>(p, ta, tb, st);
+    case kModeRaw: return launch_mode<kModeRaw>(p, ta, tb, st);
+    case kModeGemm: return launch_mode<kModeGemm>(p, ta, tb, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace df

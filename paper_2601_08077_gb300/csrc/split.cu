@@ -188,8 +188,13 @@ __global__ void __launch_bounds__(256) split_xblocks_kernel(const double *__rest
   }
 }
 
-// K[mu][nu] = sum_b Kp[b][max(mu,nu)][min(mu,nu)] in block order (FP64).
-__global__ void kpart_reduce_kernel(const double *__restrict__ Kp, int nao, int nblk, double *__restrict__ K) {
+// K[mu][nu] = sum_b fl( 2^(eX[b,mu] + eX[b,nu] - 14 - 8(s_b - 1) + T(s_b)) * sum_sp R[b,sp] ),
+// blocks in order (FP64), where R[b,sp][hi][lo] are the exact int64 partials of
+// the second exchange GEMM (lower block-triangle, transposed) and the sum over
+// the K splits of a block is exact.
+__global__ void kpart_reduce_kernel(const long long *__restrict__ Rp, const int *__restrict__ eX,
+                                    const int *__restrict__ s_blk, ShiftTable shiftT, int nao, int nblk, int nsplit,
+                                    double *__restrict__ K) {
   const int nu = blockIdx.x * blockDim.x + threadIdx.x;
   const int mu = blockIdx.y;
   if (nu >= nao) return;
@@ -198,7 +203,13 @@ __global__ void kpart_reduce_kernel(const double *__restrict__ Kp, int nao, int 
   const long long off = (long long)hi * nao + lo;
   const long long bs = (long long)nao * nao;
   double acc = 0.0;
-  for (int b = 0; b < nblk; ++b) acc += Kp[b * bs + off];
+  for (int b = 0; b < nblk; ++b) {
+    long long R = 0;
+    for (int sp = 0; sp < nsplit; ++sp) R += Rp[((long long)b * nsplit + sp) * bs + off];
+    const int s = s_blk[b];
+    const int k = eX[b * nao + mu] + eX[b * nao + nu] - 14 - 8 * (s - 1) + shiftT.v[s];
+    acc += ldexp_i64(R, k);
+  }
   K[(long long)mu * nao + nu] = acc;
 }
 
@@ -238,9 +249,10 @@ cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_kpart_reduce(const double *Kp, int nao, int nblk, double *K, cudaStream_t st) {
+cudaError_t launch_kpart_reduce(const long long *Rp, const int *eX, const int *s_blk, ShiftTable shiftT, int nao,
+                                int nblk, int nsplit, double *K, cudaStream_t st) {
   dim3 grid((nao + 127) / 128, nao);
-  kpart_reduce_kernel<<<grid, 128, 0, st>>>(Kp, nao, nblk, K);
+  kpart_reduce_kernel<<<grid, 128, 0, st>>>(Rp, eX, s_blk, shiftT, nao, nblk, nsplit, K);
   return cudaGetLastError();
 }
 
