@@ -528,6 +528,8 @@ df_status grid_gemm(const double *A, const double *B, int M, int N, int K, int s
   if (e == cudaSuccess) e = cudaMalloc(&eb, sizeof(int) * N);
   if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  // raw mode adds every chunk into its group's output: start from zero
+  if (e == cudaSuccess && mode == df::kModeRaw) e = cudaMemsetAsync(raw, 0, sizeof(int64_t) * (size_t)s * M * N, st);
   if (e == cudaSuccess) e = df::launch_split_rows_bf16(A, M, K, K, s, ea, Ad, ld, (long long)M * ld, st);
   if (e == cudaSuccess) e = df::launch_split_rows_bf16(B, N, K, K, s, eb, Bd, ld, (long long)N * ld, st);
   if (e == cudaSuccess) {

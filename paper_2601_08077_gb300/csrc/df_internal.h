@@ -62,8 +62,8 @@ cudaError_t launch_split_rows_int8(const double *A, int rows, int cols, int ld, 
                                    int8_t *digits, cudaStream_t st);
 cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int nslices, int *exps,
                                    uint16_t *digits, long long dld, long long plane_stride, cudaStream_t st);
-cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, int nslices, int *eX,
-                                 uint16_t *Xd, long long kb_ld, int nblk, cudaStream_t st);
+cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, int nslices, int *eX, uint16_t *Xd,
+                                 long long kb_ld, int nblk, cudaStream_t st);
 struct ShiftTable {
   int v[9];
 };

@@ -42,24 +42,31 @@ namespace df {
 
 namespace {
 
-constexpr int kStages = 6;
-constexpr int kTileBytes = kTile * kKTile * 2;  // 16 KB of BF16
-constexpr int kStageBytes = 2 * kTileBytes;     // A tile + B tile
-constexpr int kThreads = 320;
+constexpr int kStages = 4;
+constexpr int kTileBytes = kTile * kKTile * 2;        // one 128 x 64 BF16 box, 16 KB
+constexpr int kStageBytes = 3 * kTileBytes;           // A_t tile + two stacked B tiles
+constexpr int kThreads = 384;                         // 12 warps
+constexpr int kEpiWarp0 = 4;
 constexpr int kEpiWarps = 8;
 constexpr int kAccBufs = 2;
-constexpr uint32_t kRCol = 256;     // int64 totals: lo words at +0..63, hi words at +64..127 per half
-constexpr int kFoldChunks = 64;     // 64 chunks x 2^24 < 2^31: int32 group sums never overflow
+constexpr uint32_t kAccCols = 256;                    // one accumulator buffer: two 128-column halves
 constexpr uint32_t kTmemCols = 512;
-constexpr int kChunkStages = kMaxChunk / kKTile;  // 16 stages = 1024 products
+constexpr int kChunkStages = kMaxChunk / kKTile;      // 16 stages = 1024 products
 constexpr uint64_t kTimeoutNs = 4000000000ull;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*alignment slack*/;
+// Register split (setmaxnreg): warps 0-3 drop to 56, the 8 epilogue warps rise
+// to 224; 128*56 + 256*224 = 64512 = 384 threads * 168 registers at launch.
+constexpr int kRegsLow = 56;
+constexpr int kRegsHigh = 224;
 
-// BF16 x BF16 -> FP32, both operands K-major, M = N = 128 (instruction
-// descriptor of tcgen05.mma .kind::f16: D fmt bits 4-5, A fmt 7-9, B fmt
-// 10-12, N>>3 at 17-22, M>>4 at 24-28).
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) |
-                            ((uint32_t)(kTile >> 4) << 24);
+// BF16 x BF16 -> FP32, both operands K-major, M = 128, N = 128 or 256
+// (instruction descriptor of tcgen05.mma .kind::f16: D fmt bits 4-5, A fmt
+// 7-9, B fmt 10-12, N>>3 at 17-22, M>>4 at 24-28).
+constexpr uint32_t idesc_for(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+constexpr uint32_t kIdesc128 = idesc_for(128);
+constexpr uint32_t kIdesc256 = idesc_for(256);
 
 struct Unit {
   int m0, n0, az0, azs, bz0, bzs, kt0, ktiles, s, blk, part;
@@ -164,17 +171,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-      : "memory");
-}
-
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
   Unit w;
@@ -226,37 +223,35 @@ __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
   return w;
 }
 
-// Epilogue store of 16 consecutive output columns n0c..n0c+15 of row m from
-// the int64 totals (lo/hi words).
+// Epilogue store of the 64 output columns n0c..n0c+63 of row m.
 template <int kMode>
-__device__ __forceinline__ void store16(const SgParams &p, const Unit &w, int m, int n0c, const uint32_t (&lo)[16],
-                                        const uint32_t (&hi)[16], int kexp_base, int ea_m) {
-  if (m >= p.m_valid) return;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int n = n0c + j;
-    if (n >= p.n_valid) continue;
-    const long long R = (long long)(((uint64_t)hi[j] << 32) | (uint64_t)lo[j]);
-    if (kMode == kModeX) {
-      p.out[(long long)n * p.out_ld + m] = ldexp_i64(R, kexp_base + ea_m + p.eb[n]);
-    } else if (kMode == kModeKPart) {
-      p.raw[(long long)w.part * p.out_blk + (long long)n * p.out_ld + m] = R;
-    } else {
-      p.out[(long long)m * p.out_ld + n] = ldexp_i64(R, kexp_base + ea_m + p.eb[n]);
-    }
-  }
-}
-
-// Raw mode: the exact group sum S_g of 64 consecutive columns.
-__device__ __forceinline__ void store_raw(const SgParams &p, int m, int n0c, int g, const int (&S)[64]) {
+__device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m, int n0c, const long long (&R)[64],
+                                        int kexp_base, int ea_m) {
   if (m >= p.m_valid) return;
 #pragma unroll
   for (int j = 0; j < 64; ++j) {
     const int n = n0c + j;
-    if (n < p.n_valid) p.raw[((long long)g * p.n_valid + n) * p.m_valid + m] = (long long)S[j];
+    if (n >= p.n_valid) continue;
+    if (kMode == kModeX) {
+      p.out[(long long)n * p.out_ld + m] = ldexp_i64(R[j], kexp_base + ea_m + p.eb[n]);
+    } else if (kMode == kModeKPart) {
+      p.raw[(long long)w.part * p.out_blk + (long long)n * p.out_ld + m] = R[j];
+    } else if (kMode == kModeGemm) {
+      p.out[(long long)m * p.out_ld + n] = ldexp_i64(R[j], kexp_base + ea_m + p.eb[n]);
+    }
   }
 }
 
+__device__ __forceinline__ long long weigh(int v, int sh) {
+  const long long x = (long long)v;
+  return sh >= 0 ? (x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
+}
+
+// The work of one unit is a sequence of "slots": for t = 0..s-1, u0 = 0, 2, 4, ...
+// <= s-1-t, the slot computes the slice pairs (t, u0) and, if u0+1 <= s-1-t,
+// (t, u0+1) with one N = 256 MMA per K step (B operand = B_u0 stacked on
+// B_u0+1); a single pair uses N = 128.  Each slot runs over all K tiles of
+// the unit in chunks of at most 16 stages (1024 products per accumulator).
 template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
@@ -298,13 +293,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
         const Unit w = decode_unit(p, u);
-        for (int g = 0; g < w.s && ok; ++g) {
-          for (int t = 0; t <= g && ok; ++t) {
+        for (int t = 0; t < w.s && ok; ++t) {
+          for (int u0 = 0; u0 <= w.s - 1 - t && ok; u0 += 2) {
+            const bool two = u0 + 1 <= w.s - 1 - t;
             for (int kt = 0; kt < w.ktiles; ++kt) {
               const uint32_t stage = it % kStages;
               const uint32_t ph = (it / kStages) & 1;
@@ -314,9 +311,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               uint8_t *sa = smem + stage * kStageBytes;
               uint8_t *sb = sa + kTileBytes;
-              mbar_expect_tx(&full[stage], kStageBytes);
-              tma_load_3d(sa, &tmap_a, &full[stage], (w.kt0 + kt) * kKTile, w.m0, w.az0 + t * w.azs);
-              tma_load_3d(sb, &tmap_b, &full[stage], (w.kt0 + kt) * kKTile, w.n0, w.bz0 + (g - t) * w.bzs);
+              const int kc = (w.kt0 + kt) * kKTile;
+              mbar_expect_tx(&full[stage], two ? 3 * kTileBytes : 2 * kTileBytes);
+              tma_load_3d(sa, &tmap_a, &full[stage], kc, w.m0, w.az0 + t * w.azs);
+              tma_load_3d(sb, &tmap_b, &full[stage], kc, w.n0, w.bz0 + u0 * w.bzs);
+              if (two) tma_load_3d(sb + kTileBytes, &tmap_b, &full[stage], kc, w.n0, w.bz0 + (u0 + 1) * w.bzs);
               ++it;
             }
           }
@@ -331,13 +330,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
     uint32_t it = 0, qc = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
       const Unit w = decode_unit(p, u);
-      for (int g = 0; g < w.s && ok; ++g) {
-        int chunk_pos = 0;
-        for (int t = 0; t <= g && ok; ++t) {
+      for (int t = 0; t < w.s && ok; ++t) {
+        for (int u0 = 0; u0 <= w.s - 1 - t && ok; u0 += 2) {
+          const bool two = u0 + 1 <= w.s - 1 - t;
+          const uint32_t idesc = two ? kIdesc256 : kIdesc128;
+          int chunk_pos = 0;
           for (int kt = 0; kt < w.ktiles; ++kt) {
             const uint32_t stage = it % kStages;
             const uint32_t ph = (it / kStages) & 1;
@@ -357,18 +359,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) {
               const uint32_t sa = smem_u32(smem + stage * kStageBytes);
               const uint32_t sb = sa + kTileBytes;
-              const uint32_t dt = tmem_base + buf * kTile;
+              const uint32_t dt = tmem_base + buf * kAccCols;
 #pragma unroll
               for (int k = 0; k < kKTile / 16; ++k)
-                umma_bf16(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), kIdesc,
+                umma_bf16(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc,
                           (chunk_pos > 0 || k > 0) ? 1u : 0u);
               umma_commit(&empty[stage]);
             }
             __syncwarp();
             ++it;
             ++chunk_pos;
-            const bool group_end = (t == g) && (kt == w.ktiles - 1);
-            if (chunk_pos == kChunkStages || group_end) {
+            if (chunk_pos == kChunkStages || kt == w.ktiles - 1) {
               if (lane == 0) umma_commit(&acc_full[buf]);
               __syncwarp();
               ++qc;
@@ -385,15 +386,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       wait_bounded(done, (qc / kAccBufs) & 1, abort_flag, p.status, false);
     }
     __syncwarp();
+  } else if (warp < kEpiWarp0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
   } else {
     // ------------------------------------------------------------ epilogue
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int half = (warp - kEpiWarp0) >> 2;
     const int row = quad * 32 + lane;
-    const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
-    const uint32_t acc_addr = lane_base + (uint32_t)(half * 64);
-    const uint32_t r_addr = lane_base + kRCol + (uint32_t)(half * 128);
-    int S[64];
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
+    long long R[64];
     uint32_t qc = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
@@ -405,87 +407,85 @@ __global__ void __launch_bounds__(kThreads, 1)
       int ea_m = 0;
       if ((kMode == kModeX || kMode == kModeGemm) && m < p.m_valid) ea_m = p.ea[m];
       const int kexp_base = -14 - 8 * (s - 1) + T;
-      bool r_zero = true;  // the int64 totals of this unit start at zero
-      for (int g = 0; g < s && ok; ++g) {
-        const int nst = (g + 1) * w.ktiles;
-        const int nch = (nst + kChunkStages - 1) / kChunkStages;
-        const int sh = 8 * (s - 1 - g) - T;
 #pragma unroll
-        for (int j = 0; j < 64; ++j) S[j] = 0;
-        for (int c = 0; c < nch; ++c) {
-          const uint32_t buf = qc % kAccBufs;
-          if (!wait_bounded(&acc_full[buf], (qc / kAccBufs) & 1, abort_flag, p.status)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            uint32_t a0[16], a1[16];
-            tmem_ld16(acc_addr + buf * kTile + hh * 32, a0);
-            tmem_ld16(acc_addr + buf * kTile + hh * 32 + 16, a1);
-            tmem_wait_ld();
-            if (hh == 1) {
-              // the whole buffer is in registers: hand it back to the MMA warp
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      for (int j = 0; j < 64; ++j) R[j] = 0;
+      const int nch = (w.ktiles + kChunkStages - 1) / kChunkStages;
+      for (int t = 0; t < s && ok; ++t) {
+        for (int u0 = 0; u0 <= s - 1 - t && ok; u0 += 2) {
+          const bool two = u0 + 1 <= s - 1 - t;
+          const int g0 = t + u0;
+          const int sh0 = kMode == kModeRaw ? 0 : 8 * (s - 1 - g0) - T;
+          const int sh1 = sh0 - 8;
+          for (int c = 0; c < nch; ++c) {
+            const uint32_t buf = qc % kAccBufs;
+            if (!wait_bounded(&acc_full[buf], (qc / kAccBufs) & 1, abort_flag, p.status)) {
+              ok = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t acc = lane_base + buf * kAccCols;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              S[hh * 32 + j] += __float2int_rz(__uint_as_float(a0[j]));
-              S[hh * 32 + 16 + j] += __float2int_rz(__uint_as_float(a1[j]));
-            }
-          }
-          ++qc;
-          const bool fold = (c == nch - 1) || ((c + 1) % kFoldChunks == 0);
-          if (kMode != kModeRaw && fold) {
-            // R += S << sh (or rounded >> -sh), 16 columns at a time
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              uint32_t lo[16], hi[16];
-              if (!r_zero) {
-                tmem_ld16(r_addr + q * 16, lo);
-                tmem_ld16(r_addr + 64 + q * 16, hi);
-                tmem_wait_ld();
+            for (int hh = 0; hh < 2; ++hh) {
+              uint32_t a0[16], a1[16], b0[16], b1[16];
+              tmem_ld16(acc + hh * 32, a0);
+              tmem_ld16(acc + hh * 32 + 16, a1);
+              if (two) {
+                tmem_ld16(acc + 128 + hh * 32, b0);
+                tmem_ld16(acc + 128 + hh * 32 + 16, b1);
               }
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const long long v = (long long)S[q * 16 + j];
-                const long long add = sh >= 0 ? (v << sh) : ((v + (1ll << (-sh - 1))) >> (-sh));
-                const long long R =
-                    (r_zero ? 0ll : (long long)(((uint64_t)hi[j] << 32) | (uint64_t)lo[j])) + add;
-                lo[j] = (uint32_t)((uint64_t)R & 0xFFFFFFFFull);
-                hi[j] = (uint32_t)((uint64_t)R >> 32);
-                S[q * 16 + j] = 0;
-              }
-              tmem_st16(r_addr + q * 16, lo);
-              tmem_st16(r_addr + 64 + q * 16, hi);
-            }
-            tmem_wait_st();
-            r_zero = false;
-          }
-        }
-        if (!ok) break;
-        if (kMode == kModeRaw) {
-          store_raw(p, m, n_base, g, S);
-        } else if (g == s - 1) {
-          // the unit is complete: scale and store the int64 totals
-#pragma unroll 1
-          for (int q = 0; q < 4; ++q) {
-            uint32_t lo[16], hi[16];
-            if (!r_zero) {
-              tmem_ld16(r_addr + q * 16, lo);
-              tmem_ld16(r_addr + 64 + q * 16, hi);
               tmem_wait_ld();
-            } else {
+              if (hh == 1) {
+                // the chunk is in registers: hand the buffer back to the MMA warp
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+              }
+              if (kMode == kModeRaw) {
+                if (m < p.m_valid) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) lo[j] = hi[j] = 0u;
+                  for (int j = 0; j < 32; ++j) {
+                    const int n = n_base + hh * 32 + j;
+                    if (n >= p.n_valid) continue;
+                    const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
+                    p.raw[((long long)g0 * p.n_valid + n) * p.m_valid + m] += (long long)v0;
+                    if (two) {
+                      const int v1 = __float2int_rz(__uint_as_float(j < 16 ? b0[j] : b1[j - 16]));
+                      p.raw[((long long)(g0 + 1) * p.n_valid + n) * p.m_valid + m] += (long long)v1;
+                    }
+                  }
+                }
+              } else if (two && sh1 >= 0) {
+                // both weights are non-negative powers of two, 2^8 apart:
+                // v0 2^sh0 + v1 2^sh1 = (v0 2^8 + v1) 2^sh1, exact in int64
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
+                  const int v1 = __float2int_rz(__uint_as_float(j < 16 ? b0[j] : b1[j - 16]));
+                  const long long w2 = ((long long)v0 << 8) + (long long)v1;
+                  R[hh * 32 + j] += w2 << sh1;
+                }
+              } else if (!two && sh0 >= 0) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
+                  R[hh * 32 + j] += (long long)v0 << sh0;
+                }
+              } else {
+                // some low-order group falls below the kept bits (T > 0): rounded shifts
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
+                  long long add = weigh(v0, sh0);
+                  if (two) add += weigh(__float2int_rz(__uint_as_float(j < 16 ? b0[j] : b1[j - 16])), sh1);
+                  R[hh * 32 + j] += add;
+                }
+              }
             }
-            store16<kMode>(p, w, m, n_base + q * 16, lo, hi, kexp_base, ea_m);
+            ++qc;
           }
         }
       }
+      if (ok && kMode != kModeRaw) store64<kMode>(p, w, m, n_base, R, kexp_base, ea_m);
     }
   }
 

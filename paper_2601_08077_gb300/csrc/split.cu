@@ -138,11 +138,13 @@ __global__ void split_cols_bf16_kernel(const double *__restrict__ C, int nrows, 
 
 // One CTA per (block b, row mu) of X [naux][nao][nocc]: the row of the second
 // exchange GEMM is X_b[mu, (P_local, i)], length nP*nocc, padded with zero
-// digits up to a multiple of 64.  Exponent per (block, mu).
+// digits up to a multiple of 64, one exponent per (block, mu).  The first pass
+// finds max|X| (from DRAM), the second re-reads the row (256 KB at most, from
+// L2) and writes the digits.  Two consecutive orbitals per thread (16-byte
+// loads, 4-byte stores) when nocc is even.
 __global__ void __launch_bounds__(256) split_xblocks_kernel(const double *__restrict__ X, int naux, int nao,
                                                             int nocc, int nslices, int *__restrict__ eX,
-                                                            uint16_t *__restrict__ Xd, long long kb_ld,
-                                                            int nblk) {
+                                                            uint16_t *__restrict__ Xd, long long kb_ld, int nblk) {
   const int mu = blockIdx.x;
   const int b = blockIdx.y;
   const int p0 = b * kBlock;
@@ -150,41 +152,79 @@ __global__ void __launch_bounds__(256) split_xblocks_kernel(const double *__rest
   const int klen = nP * nocc;
   const int kpad = (klen + 63) / 64 * 64;
   __shared__ uint64_t red[8];
-  uint64_t m = 0;
-  for (int pl = 0; pl < nP; ++pl) {
-    const double *src = X + ((long long)(p0 + pl) * nao + mu) * nocc;
-    for (int i = threadIdx.x; i < nocc; i += blockDim.x) {
-      uint64_t a = abs_bits(src[i]);
-      m = a > m ? a : m;
+  __shared__ int e_sh;
+  {
+    uint64_t m = 0;
+    if ((nocc & 1) == 0) {
+      const int hp = nocc >> 1;
+      for (int q = threadIdx.x; q < nP * hp; q += blockDim.x) {
+        const int pl = q / hp;
+        const int i = 2 * (q - pl * hp);
+        const double2 v = *reinterpret_cast<const double2 *>(X + ((long long)(p0 + pl) * nao + mu) * nocc + i);
+        const uint64_t a = abs_bits(v.x), c = abs_bits(v.y);
+        m = a > m ? a : m;
+        m = c > m ? c : m;
+      }
+    } else {
+      for (int k = threadIdx.x; k < klen; k += blockDim.x) {
+        const int pl = k / nocc;
+        const uint64_t a = abs_bits(X[((long long)(p0 + pl) * nao + mu) * nocc + (k - pl * nocc)]);
+        m = a > m ? a : m;
+      }
     }
+    m = warp_max_u64(m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint64_t v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+      v = warp_max_u64(v);
+      if (threadIdx.x == 0) {
+        e_sh = exponent_from_max_bits_dev(v);
+        eX[b * nao + mu] = e_sh;
+      }
+    }
+    __syncthreads();
   }
-  m = warp_max_u64(m);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint64_t v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-    v = warp_max_u64(v);
-    if (threadIdx.x == 0) red[0] = v;
-  }
-  __syncthreads();
-  const int e = exponent_from_max_bits_dev(red[0]);
-  if (threadIdx.x == 0) eX[b * nao + mu] = e;
+  const int e = e_sh;
   const long long plane = (long long)nblk * nao * kb_ld;
   uint16_t *dst = Xd + ((long long)b * nao + mu) * kb_ld;
-  for (int k = threadIdx.x; k < kpad; k += blockDim.x) {
-    int d[kSMax];
-    if (k < klen) {
-      int pl = k / nocc;
-      int i = k - pl * nocc;
-      double v = X[((long long)(p0 + pl) * nao + mu) * nocc + i];
-      balanced_digits(scaled_rne((uint64_t)__double_as_longlong(v), e), d);
-    } else {
+  if ((nocc & 1) == 0) {
+    const int hp = nocc >> 1;
+    for (int q = threadIdx.x; 2 * q < kpad; q += blockDim.x) {
+      const int k = 2 * q;
+      int d0[kSMax], d1[kSMax];
+      if (k < klen) {
+        const int pl = q / hp;
+        const int i = k - pl * nocc;
+        const double2 v = *reinterpret_cast<const double2 *>(X + ((long long)(p0 + pl) * nao + mu) * nocc + i);
+        balanced_digits(scaled_rne((uint64_t)__double_as_longlong(v.x), e), d0);
+        balanced_digits(scaled_rne((uint64_t)__double_as_longlong(v.y), e), d1);
+      } else {
 #pragma unroll
-      for (int t = 0; t < kSMax; ++t) d[t] = 0;
+        for (int t = 0; t < kSMax; ++t) d0[t] = d1[t] = 0;
+      }
+#pragma unroll
+      for (int t = 0; t < kSMax; ++t)
+        if (t < nslices)
+          *reinterpret_cast<uint32_t *>(dst + (long long)t * plane + k) =
+              (uint32_t)int_to_bf16_bits(d0[t]) | ((uint32_t)int_to_bf16_bits(d1[t]) << 16);
     }
+  } else {
+    for (int k = threadIdx.x; k < kpad; k += blockDim.x) {
+      int d[kSMax];
+      if (k < klen) {
+        const int pl = k / nocc;
+        const int i = k - pl * nocc;
+        balanced_digits(scaled_rne((uint64_t)__double_as_longlong(X[((long long)(p0 + pl) * nao + mu) * nocc + i]), e),
+                        d);
+      } else {
 #pragma unroll
-    for (int t = 0; t < kSMax; ++t)
-      if (t < nslices) dst[(long long)t * plane + k] = int_to_bf16_bits(d[t]);
+        for (int t = 0; t < kSMax; ++t) d[t] = 0;
+      }
+#pragma unroll
+      for (int t = 0; t < kSMax; ++t)
+        if (t < nslices) dst[(long long)t * plane + k] = int_to_bf16_bits(d[t]);
+    }
   }
 }
 
@@ -242,8 +282,8 @@ cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int ns
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, int nslices, int *eX,
-                                 uint16_t *Xd, long long kb_ld, int nblk, cudaStream_t st) {
+cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, int nslices, int *eX, uint16_t *Xd,
+                                 long long kb_ld, int nblk, cudaStream_t st) {
   dim3 grid(nao, nblk);
   split_xblocks_kernel<<<grid, 256, 0, st>>>(X, naux, nao, nocc, nslices, eX, Xd, kb_ld, nblk);
   return cudaGetLastError();
