@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["small", "profile", "medium", "large"], default="medium")
+    ap.add_argument("--workload", choices=["small", "profile", "medium", "large", "batch"], default="medium")
+    ap.add_argument("--batch-size", type=int, default=48)
     ap.add_argument("--nslices", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -171,11 +172,84 @@ def run_reference(args, w):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batch(args):
+    """Grouped batch: molecules of 30..120 atoms (nao 150..600, naux 3 nao, nocc nao/5), all
+    exchange builds in grouped persistent launches captured as one CUDA graph, against one
+    native-FP64 build per molecule on the same GPU."""
+    import torch
+    from paper_2601_08077_gb300 import build, df, inputs
+    build.build_all()
+    torch.cuda.set_device(0)
+    ws = inputs.batch_workloads(args.batch_size)
+    s = args.nslices
+    t0 = time.perf_counter()
+    ctxs, Bs, Cs, Ds = [], [], [], []
+    for w in ws:
+        mol = inputs.molecule(w.n_atoms, w.seed)
+        B = inputs.df_tensor_device(mol)
+        C = inputs.orbitals(mol.nao, w.nocc, w.seed + 1)
+        ctx = df.Context(mol.nao, mol.naux, w.nocc, s_max=s)
+        ctx.setup(B)
+        ctxs.append(ctx)
+        Bs.append(B)
+        Cs.append(torch.from_numpy(C).cuda())
+        Ds.append(torch.from_numpy(inputs.density(C)).cuda())
+    gen_s = time.perf_counter() - t0
+    Ks = [torch.empty((c.nao, c.nao), dtype=torch.float64, device="cuda") for c in ctxs]
+    Js = [torch.empty_like(k) for k in Ks]
+    batch = df.Batch(ctxs)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        choice = batch.autotune(Cs, s, Ks)
+        for _ in range(args.warmup):
+            batch.build_J(Ds, Js)
+            batch.build_K(Cs, s, Ks)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        with Clocks(0) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                batch.build_J(Ds, Js)
+                batch.build_K(Cs, s, Ks)
+            e1.record(stream)
+            stream.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    FK = sum(4.0 * w.nao ** 2 * w.naux * w.nocc for w in ws)
+    # accuracy of the batch against the FP64 build, and the FP64 builds' time (one per molecule)
+    worst = 0.0
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K64 = [torch.empty_like(k) for k in Ks]
+    f0.record()
+    for ctx, C, K in zip(ctxs, Cs, K64):
+        ctx.build_K(C, 0, K)
+    f1.record()
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    for K, K0 in zip(Ks, K64):
+        worst = max(worst, float((K - K0).abs().max() / K0.abs().max()))
+    return {"metric": "batched DF J/K builds, molecules/s and effective FP64 TFLOP/s", "value": FK / (ms * 1e-3) / 1e12,
+            "unit": UNIT, "molecules_per_s": len(ws) / (ms * 1e-3), "n_molecules": len(ws), "ms_per_batch": ms,
+            "steps": args.steps, "warmup": args.warmup, "nslices": s, "autotune": {"ksplit_cap": choice[0],
+                                                                                 "order": choice[1]},
+            "fp64_per_molecule": {"ms_per_batch": ms64, "tflops": FK / (ms64 * 1e-3) / 1e12,
+                                  "molecules_per_s": len(ws) / (ms64 * 1e-3)},
+            "max_dK_rel_vs_fp64": worst, "generation_s": gen_s,
+            "config": {"workload": "batch-%d-molecules-30to120-atoms" % len(ws), "nao": [w.nao for w in ws],
+                       "naux_per_nao": 3, "nocc": "nao/5"},
+            "clocks": clk.summary()}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "batch":
+        if rank == 0:
+            print(json.dumps(run_batch(args)), flush=True)
+        return
     w = workload(args.workload)
 
     if args.impl == "reference":

@@ -152,6 +152,32 @@ df_status df_sync_status(df_ctx *ctx, void *stream);
 df_status df_last_error(const df_ctx *ctx);
 const char *df_strerror(df_status s);
 
+/* ---- Batched builds over many molecules (grouped persistent launches) ----
+ * A batch groups n contexts that are already set up (one molecule each, of
+ * any size).  df_batch_build_K runs, for all molecules at once: the C
+ * splits, ONE persistent launch of the first exchange GEMM over the work
+ * units of every molecule, the X splits, ONE persistent launch of the second
+ * GEMM, and the reductions (Section 3.3 blocking per molecule, Section 3.2
+ * emulation).  With graphs on (the default) the whole sequence is captured
+ * once per (nslices, argument pointers) as a CUDA graph and replayed; a NULL
+ * stream runs it without a graph.  Pointer arrays are host arrays of device
+ * pointers, one per molecule.  The caller keeps the contexts alive. */
+typedef struct df_batch df_batch;
+df_status df_batch_create(df_batch **out, df_ctx *const *ctxs, int n);
+void df_batch_destroy(df_batch *b);
+df_status df_batch_set_graphs(df_batch *b, int on);
+df_status df_batch_build_K(df_batch *b, const double *const *C_dev, const int *nocc, int nslices,
+                           double *const *K_dev, void *stream);
+/* FP64 Coulomb build of every molecule (Eqs. df-j-1/2), graph-captured likewise;
+ * rho goes to each context's internal buffer. */
+df_status df_batch_build_J(df_batch *b, const double *const *D_dev, double *const *J_dev, void *stream);
+/* Autotuner: times the K-split depth of the second GEMM (1, 2 or the
+ * context's maximum) and the molecule order of the unit lists (as given, or
+ * most expensive first) on this batch and keeps the fastest; choice[0] =
+ * K-split cap, choice[1] = order.  Synchronises `stream`. */
+df_status df_batch_autotune(df_batch *b, const double *const *C_dev, const int *nocc, int nslices,
+                            double *const *K_dev, void *stream, int *choice);
+
 /* Phases timed when profiling is on (CUDA events on the call's stream). */
 #define DF_PHASE_SPLIT_C 0  /* C -> digit planes */
 #define DF_PHASE_GEMM1 1    /* X = B C on the tensor cores (or cuBLAS DGEMM in FP64 mode) */

@@ -16,38 +16,7 @@
 #include <cstring>
 #include <new>
 
-struct df_ctx {
-  int nao = 0, naux = 0, nocc_max = 0, s_max = 0, nblk = 0;
-  long long ld_nao = 0;    // row stride (elements) of the B and C digit rows
-  long long kb_ld_max = 0; // row stride bound of the X digit rows
-  const double *B = nullptr;
-  bool ready = false;
-  uint16_t *Bd = nullptr;
-  int *eB = nullptr;
-  uint16_t *Cd = nullptr;
-  int *eC = nullptr;
-  double *X = nullptr;
-  uint16_t *Xd = nullptr;
-  int *eX = nullptr;
-  long long *Rp = nullptr;  // int64 partials of the second GEMM [nblk][nsplit][nao][nao]
-  int nsplit = 1;
-  double *rho = nullptr;
-  double *epart = nullptr;
-  double *E = nullptr;
-  int *sblk = nullptr;      // device per-block slice counts
-  int *sblk_host = nullptr; // pinned mirror of the last upload
-  int *status = nullptr;
-  int64_t bytes = 0;
-  df_status last = DF_OK;
-  cublasHandle_t cublas = nullptr;
-  // per-phase event timing
-  bool profiling = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[DF_NPHASES];
-  std::vector<cudaEvent_t> pool;
-  // adaptive controller (Section 3.2)
-  int level = 4, iter = 0, fp64_from = -1;
-  double E_prev = 0.0;
-};
+#include "df_ctx.h"
 
 namespace {
 
@@ -155,6 +124,76 @@ df_status build_K_fp64(df_ctx *c, const double *C, int nocc, double *K, cudaStre
   return DF_OK;
 }
 
+}  // namespace
+
+namespace df {
+
+df_status ctx_upload_slices(df_ctx *c, const int *sb, cudaStream_t st) { return upload_slices(c, sb, st); }
+
+// Parameters and operand maps of the first exchange GEMM (X^T = C^T B^T).
+bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb) {
+  const int nao = c->nao, naux = c->naux;
+  const long long c_plane = (long long)c->nocc_max * c->ld_nao;
+  if (!make_tmap_bf16(&ta, c->Cd, nao, nocc, c->s_max, c->ld_nao, c_plane)) return false;
+  if (!make_tmap_bf16(&tb, c->Bd, nao, (long long)naux * nao, c->s_max, c->ld_nao, (long long)naux * nao * c->ld_nao))
+    return false;
+  std::memset(&p, 0, sizeof(p));
+  p.layout = kLayoutX;
+  p.mode = kModeX;
+  p.nt_m = (nocc + kTile - 1) / kTile;
+  p.nt_n = (int)(((long long)naux * nao + kTile - 1) / kTile);
+  p.nunits = p.nt_m * p.nt_n;
+  p.m_valid = nocc;
+  p.n_valid = naux * nao;
+  p.ktiles = (nao + kKTile - 1) / kKTile;
+  p.nao = nao;
+  p.nocc = nocc;
+  p.nblk = c->nblk;
+  p.naux = naux;
+  p.s_blk = c->sblk;
+  for (int q = 0; q <= 8; ++q) p.shiftT[q] = fixed_point_shift(q, (long long)p.ktiles * kKTile);
+  p.ea = c->eC;
+  p.eb = c->eB;
+  p.out = c->X;
+  p.out_ld = nocc;
+  p.status = c->status;
+  return true;
+}
+
+// Parameters and operand map of the second exchange GEMM (K_b = X_b X_b^T).
+bool gemm2_setup(df_ctx *c, int nocc, int nsplit, SgParams &q2, CUtensorMap &tx) {
+  const int nao = c->nao, naux = c->naux;
+  const long long kb_ld = round_up((long long)kBlock * nocc, 64);
+  if (!make_tmap_bf16(&tx, c->Xd, kb_ld, nao, (long long)c->s_max * c->nblk, kb_ld, (long long)nao * kb_ld))
+    return false;
+  std::memset(&q2, 0, sizeof(q2));
+  q2.layout = kLayoutKPart;
+  q2.mode = kModeKPart;
+  q2.nt_m = q2.nt_n = (nao + kTile - 1) / kTile;
+  q2.nsplit = nsplit;
+  q2.nunits = q2.nt_m * (q2.nt_m + 1) / 2 * c->nblk * nsplit;
+  q2.m_valid = q2.n_valid = nao;
+  q2.nao = nao;
+  q2.nocc = nocc;
+  q2.nblk = c->nblk;
+  q2.naux = naux;
+  q2.s_blk = c->sblk;
+  for (int q = 0; q <= 8; ++q) q2.shiftT[q] = fixed_point_shift(q, kb_ld);
+  q2.ea = c->eX;
+  q2.eb = c->eX;
+  q2.raw = c->Rp;
+  q2.out_ld = nao;
+  q2.out_blk = (long long)nao * nao;
+  q2.status = c->status;
+  return true;
+}
+
+long long xdigit_ld(int nocc) { return round_up((long long)kBlock * nocc, 64); }
+
+}  // namespace df
+
+namespace {
+
 df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, double *K, df_kstats *stats,
                            cudaStream_t st) {
   int smax = 0;
@@ -172,66 +211,23 @@ df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, 
     DF_TRY(c, df::launch_split_cols_bf16(C, nao, nocc, smax, c->eC, c->Cd, c->ld_nao, c_plane, st));
   }
   // 2. X^T = C^T B^T
-  CUtensorMap ta, tb;
-  if (!df::make_tmap_bf16(&ta, c->Cd, nao, nocc, c->s_max, c->ld_nao, c_plane)) return record(c, DF_ERR_CUDA);
-  if (!df::make_tmap_bf16(&tb, c->Bd, nao, (long long)naux * nao, c->s_max, c->ld_nao,
-                          (long long)naux * nao * c->ld_nao))
-    return record(c, DF_ERR_CUDA);
   df::SgParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.layout = df::kLayoutX;
-  p.mode = df::kModeX;
-  p.nt_m = (nocc + df::kTile - 1) / df::kTile;
-  p.nt_n = (int)(((long long)naux * nao + df::kTile - 1) / df::kTile);
-  p.nunits = p.nt_m * p.nt_n;
-  p.m_valid = nocc;
-  p.n_valid = naux * nao;
-  p.ktiles = (nao + df::kKTile - 1) / df::kKTile;
-  p.nao = nao;
-  p.nocc = nocc;
-  p.nblk = c->nblk;
-  p.naux = naux;
-  p.s_blk = c->sblk;
-  for (int q = 0; q <= 8; ++q) p.shiftT[q] = df::fixed_point_shift(q, (long long)p.ktiles * df::kKTile);
-  p.ea = c->eC;
-  p.eb = c->eB;
-  p.out = c->X;
-  p.out_ld = nocc;
-  p.status = c->status;
+  CUtensorMap ta, tb;
+  if (!df::gemm1_setup(c, nocc, p, ta, tb)) return record(c, DF_ERR_CUDA);
   {
     PhaseTimer t(c, DF_PHASE_GEMM1, st);
     DF_TRY(c, df::launch_slice_gemm(p, ta, tb, st));
   }
   // 3. X -> per-(block, mu) digit planes
-  const long long kb_ld = round_up((long long)kBlock * nocc, 64);
+  const long long kb_ld = df::xdigit_ld(nocc);
   {
     PhaseTimer t(c, DF_PHASE_SPLIT_X, st);
     DF_TRY(c, df::launch_split_xblocks(c->X, naux, nao, nocc, smax, c->eX, c->Xd, kb_ld, c->nblk, st));
   }
-  // 4. per-block K_b on upper tiles
-  CUtensorMap tx;
-  if (!df::make_tmap_bf16(&tx, c->Xd, kb_ld, nao, (long long)c->s_max * c->nblk, kb_ld, (long long)nao * kb_ld))
-    return record(c, DF_ERR_CUDA);
+  // 4. per-block K_b on upper tiles (exact int64 partials per K split)
   df::SgParams q2;
-  std::memset(&q2, 0, sizeof(q2));
-  q2.layout = df::kLayoutKPart;
-  q2.mode = df::kModeKPart;
-  q2.nt_m = q2.nt_n = (nao + df::kTile - 1) / df::kTile;
-  q2.nsplit = c->nsplit;
-  q2.nunits = q2.nt_m * (q2.nt_m + 1) / 2 * c->nblk * c->nsplit;
-  q2.m_valid = q2.n_valid = nao;
-  q2.nao = nao;
-  q2.nocc = nocc;
-  q2.nblk = c->nblk;
-  q2.naux = naux;
-  q2.s_blk = c->sblk;
-  for (int q = 0; q <= 8; ++q) q2.shiftT[q] = df::fixed_point_shift(q, kb_ld);
-  q2.ea = c->eX;
-  q2.eb = c->eX;
-  q2.raw = c->Rp;
-  q2.out_ld = nao;
-  q2.out_blk = (long long)nao * nao;
-  q2.status = c->status;
+  CUtensorMap tx;
+  if (!df::gemm2_setup(c, nocc, c->nsplit, q2, tx)) return record(c, DF_ERR_CUDA);
   {
     PhaseTimer t(c, DF_PHASE_GEMM2, st);
     DF_TRY(c, df::launch_slice_gemm(q2, tx, tx, st));

@@ -1,0 +1,50 @@
+// The context behind the opaque df_ctx handle of the C ABI (internal).
+#pragma once
+#include <utility>
+#include <vector>
+
+#include "df_internal.h"
+
+struct df_ctx {
+  int nao = 0, naux = 0, nocc_max = 0, s_max = 0, nblk = 0;
+  long long ld_nao = 0;    // row stride (elements) of the B and C digit rows
+  long long kb_ld_max = 0; // row stride bound of the X digit rows
+  const double *B = nullptr;
+  bool ready = false;
+  uint16_t *Bd = nullptr;
+  int *eB = nullptr;
+  uint16_t *Cd = nullptr;
+  int *eC = nullptr;
+  double *X = nullptr;
+  uint16_t *Xd = nullptr;
+  int *eX = nullptr;
+  long long *Rp = nullptr;  // int64 partials of the second GEMM [nblk][nsplit][nao][nao]
+  int nsplit = 1;
+  double *rho = nullptr;
+  double *epart = nullptr;
+  double *E = nullptr;
+  int *sblk = nullptr;      // device per-block slice counts
+  int *sblk_host = nullptr; // pinned mirror of the last upload
+  int *status = nullptr;
+  int64_t bytes = 0;
+  df_status last = DF_OK;
+  cublasHandle_t cublas = nullptr;
+  // per-phase event timing
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[DF_NPHASES];
+  std::vector<cudaEvent_t> pool;
+  // adaptive controller (Section 3.2)
+  int level = 4, iter = 0, fp64_from = -1;
+  double E_prev = 0.0;
+};
+
+
+namespace df {
+// Upload per-block slice counts to the context if they changed (synchronises
+// the stream when they did; not allowed during stream capture).
+df_status ctx_upload_slices(df_ctx *c, const int *sb, cudaStream_t st);
+// Parameters and operand maps of the two exchange GEMMs of a context.
+bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb);
+bool gemm2_setup(df_ctx *c, int nocc, int nsplit, SgParams &q2, CUtensorMap &tx);
+long long xdigit_ld(int nocc);
+}  // namespace df

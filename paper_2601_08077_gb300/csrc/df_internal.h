@@ -52,6 +52,18 @@ struct SgParams {
   int *status;              // device status word (DF_ERR_TIMEOUT bits)
 };
 
+// A grouped launch: the work units of several problems (molecules) in one
+// persistent launch.  Problem i owns units [unit_off[i], unit_off[i+1]); its
+// parameters are params[i] and its operand tensor maps maps[2i] (A side) and
+// maps[2i+1] (B side), all in device memory (maps 64-byte aligned).
+struct SgGroup {
+  const SgParams *params;
+  const CUtensorMap *maps;
+  const int *unit_off;
+  int nmol;
+  int total;
+};
+
 struct Ctx;
 
 // Kernel launchers (split.cu, slicegemm.cu, coulomb.cu).
@@ -76,6 +88,8 @@ bool make_tmap_bf16(CUtensorMap *map, const void *base, long long k, long long r
 
 cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb,
                               cudaStream_t st);
+// Grouped launch; `mode` is shared by all problems, `grid` CTAs (0 = one per SM).
+cudaError_t launch_slice_gemm_grouped(int mode, const SgGroup &g, int *status, int grid, cudaStream_t st);
 int slice_gemm_grid(int nunits);
 int fixed_point_shift(int s, long long k);
 

@@ -37,6 +37,7 @@
 #include "df_internal.h"
 
 #include <cstdio>
+#include <cstring>
 
 namespace df {
 
@@ -252,10 +253,33 @@ __device__ __forceinline__ long long weigh(int v, int sh) {
 // (t, u0+1) with one N = 256 MMA per K step (B operand = B_u0 stacked on
 // B_u0+1); a single pair uses N = 128.  Each slot runs over all K tiles of
 // the unit in chunks of at most 16 stages (1024 products per accumulator).
-template <int kMode>
+// Parameters and operand maps of global unit u: the launch's own (single
+// problem) or, in a grouped launch, those of the problem that owns u.
+template <bool kGrouped>
+__device__ __forceinline__ const SgParams &unit_params(const SgParams &p, const SgGroup &g, int u, int &local,
+                                                      int &mol) {
+  if (!kGrouped) {
+    local = u;
+    mol = 0;
+    return p;
+  }
+  int lo = 0, hi = g.nmol - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.unit_off[mid] <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  mol = lo;
+  local = u - g.unit_off[lo];
+  return g.params[lo];
+}
+
+template <int kMode, bool kGrouped>
 __global__ void __launch_bounds__(kThreads, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
-                      const SgParams p) {
+                      const SgParams p, const SgGroup grp) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
@@ -290,6 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const int total_units = kGrouped ? grp.total : p.nunits;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -297,8 +322,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
-        const Unit w = decode_unit(p, u);
+      for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+        int lu, mol;
+        const SgParams &q = unit_params<kGrouped>(p, grp, u, lu, mol);
+        const Unit w = decode_unit(q, lu);
+        const CUtensorMap *ma = kGrouped ? &grp.maps[2 * mol] : &tmap_a;
+        const CUtensorMap *mb = kGrouped ? &grp.maps[2 * mol + 1] : &tmap_b;
         for (int t = 0; t < w.s && ok; ++t) {
           for (int u0 = 0; u0 <= w.s - 1 - t && ok; u0 += 2) {
             const bool two = u0 + 1 <= w.s - 1 - t;
@@ -313,9 +342,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint8_t *sb = sa + kTileBytes;
               const int kc = (w.kt0 + kt) * kKTile;
               mbar_expect_tx(&full[stage], two ? 3 * kTileBytes : 2 * kTileBytes);
-              tma_load_3d(sa, &tmap_a, &full[stage], kc, w.m0, w.az0 + t * w.azs);
-              tma_load_3d(sb, &tmap_b, &full[stage], kc, w.n0, w.bz0 + u0 * w.bzs);
-              if (two) tma_load_3d(sb + kTileBytes, &tmap_b, &full[stage], kc, w.n0, w.bz0 + (u0 + 1) * w.bzs);
+              tma_load_3d(sa, ma, &full[stage], kc, w.m0, w.az0 + t * w.azs);
+              tma_load_3d(sb, mb, &full[stage], kc, w.n0, w.bz0 + u0 * w.bzs);
+              if (two) tma_load_3d(sb + kTileBytes, mb, &full[stage], kc, w.n0, w.bz0 + (u0 + 1) * w.bzs);
               ++it;
             }
           }
@@ -333,8 +362,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
     uint32_t it = 0, qc = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
-      const Unit w = decode_unit(p, u);
+    for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+      int lu, mol;
+      const SgParams &q = unit_params<kGrouped>(p, grp, u, lu, mol);
+      const Unit w = decode_unit(q, lu);
       for (int t = 0; t < w.s && ok; ++t) {
         for (int u0 = 0; u0 <= w.s - 1 - t && ok; u0 += 2) {
           const bool two = u0 + 1 <= w.s - 1 - t;
@@ -398,14 +429,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     long long R[64];
     uint32_t qc = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
-      const Unit w = decode_unit(p, u);
+    for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+      int lu, mol;
+      const SgParams &q = unit_params<kGrouped>(p, grp, u, lu, mol);
+      const Unit w = decode_unit(q, lu);
       const int s = w.s;
-      const int T = kMode == kModeRaw ? 0 : p.shiftT[s];
+      const int T = kMode == kModeRaw ? 0 : q.shiftT[s];
       const int m = w.m0 + row;
       const int n_base = w.n0 + half * 64;
       int ea_m = 0;
-      if ((kMode == kModeX || kMode == kModeGemm) && m < p.m_valid) ea_m = p.ea[m];
+      if ((kMode == kModeX || kMode == kModeGemm) && m < q.m_valid) ea_m = q.ea[m];
       const int kexp_base = -14 - 8 * (s - 1) + T;
 #pragma unroll
       for (int j = 0; j < 64; ++j) R[j] = 0;
@@ -441,16 +474,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
               }
               if (kMode == kModeRaw) {
-                if (m < p.m_valid) {
+                if (m < q.m_valid) {
 #pragma unroll
                   for (int j = 0; j < 32; ++j) {
                     const int n = n_base + hh * 32 + j;
-                    if (n >= p.n_valid) continue;
+                    if (n >= q.n_valid) continue;
                     const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
-                    p.raw[((long long)g0 * p.n_valid + n) * p.m_valid + m] += (long long)v0;
+                    q.raw[((long long)g0 * q.n_valid + n) * q.m_valid + m] += (long long)v0;
                     if (two) {
                       const int v1 = __float2int_rz(__uint_as_float(j < 16 ? b0[j] : b1[j - 16]));
-                      p.raw[((long long)(g0 + 1) * p.n_valid + n) * p.m_valid + m] += (long long)v1;
+                      q.raw[((long long)(g0 + 1) * q.n_valid + n) * q.m_valid + m] += (long long)v1;
                     }
                   }
                 }
@@ -485,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      if (ok && kMode != kModeRaw) store64<kMode>(p, w, m, n_base, R, kexp_base, ea_m);
+      if (ok && kMode != kModeRaw) store64<kMode>(q, w, m, n_base, R, kexp_base, ea_m);
     }
   }
 
@@ -557,26 +590,46 @@ int slice_gemm_grid(int nunits) {
   return nunits < nsm ? nunits : nsm;
 }
 
-template <int kMode>
-cudaError_t launch_mode(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
+template <int kMode, bool kGrouped>
+cudaError_t launch_mode(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, const SgGroup &g, int grid,
+                        cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(slice_gemm_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<kMode, kGrouped>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  slice_gemm_kernel<kMode><<<slice_gemm_grid(p.nunits), kThreads, kSmemBytes, st>>>(ta, tb, p);
+  slice_gemm_kernel<kMode, kGrouped><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, p, g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
   if (p.nunits <= 0) return cudaSuccess;
+  SgGroup g;
+  std::memset(&g, 0, sizeof(g));
+  const int grid = slice_gemm_grid(p.nunits);
   switch (p.mode) {
-    case kModeX: return launch_mode<kModeX>(p, ta, tb, st);
-    case kModeKPart: return launch_mode<kModeKPart>(p, ta, tb, st);
-    case kModeRaw: return launch_mode<kModeRaw>(p, ta, tb, st);
-    case kModeGemm: return launch_mode<kModeGemm>(p, ta, tb, st);
+    case kModeX: return launch_mode<kModeX, false>(p, ta, tb, g, grid, st);
+    case kModeKPart: return launch_mode<kModeKPart, false>(p, ta, tb, g, grid, st);
+    case kModeRaw: return launch_mode<kModeRaw, false>(p, ta, tb, g, grid, st);
+    case kModeGemm: return launch_mode<kModeGemm, false>(p, ta, tb, g, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_slice_gemm_grouped(int mode, const SgGroup &g, int *status, int grid, cudaStream_t st) {
+  if (g.total <= 0) return cudaSuccess;
+  SgParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.status = status;
+  CUtensorMap dummy;
+  std::memset(&dummy, 0, sizeof(dummy));
+  const int full_grid = slice_gemm_grid(g.total);
+  const int gsz = grid > 0 && grid < full_grid ? grid : full_grid;
+  switch (mode) {
+    case kModeX: return launch_mode<kModeX, true>(p, dummy, dummy, g, gsz, st);
+    case kModeKPart: return launch_mode<kModeKPart, true>(p, dummy, dummy, g, gsz, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -70,6 +70,14 @@ def lib():
         L.df_strerror.restype = ctypes.c_char_p
         L.df_set_profiling.argtypes = [P, I]
         L.df_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        L.df_batch_create.argtypes = [pp, PP, I]
+        L.df_batch_destroy.argtypes = [P]
+        L.df_batch_destroy.restype = None
+        L.df_batch_set_graphs.argtypes = [P, I]
+        L.df_batch_build_K.argtypes = [P, PP, ctypes.POINTER(ctypes.c_int), I, PP, V]
+        L.df_batch_build_J.argtypes = [P, PP, PP, V]
+        L.df_batch_autotune.argtypes = [P, PP, ctypes.POINTER(ctypes.c_int), I, PP, V, ctypes.POINTER(ctypes.c_int)]
         L.df_workspace_bytes.argtypes = [P]
         L.df_workspace_bytes.restype = ctypes.c_int64
         _lib = L
@@ -228,3 +236,50 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(lib().df_sync_status(self._h, _stream(stream)), "df_sync_status")
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _f64(t)
+    return arr
+
+
+class Batch:
+    """Batched J/K builds over several contexts (grouped persistent launches + CUDA graphs)."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        handles = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        _check(lib().df_batch_create(ctypes.byref(h), handles, len(self.contexts)), "df_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().df_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_graphs(self, on: bool):
+        _check(lib().df_batch_set_graphs(self._h, 1 if on else 0), "df_batch_set_graphs")
+
+    def build_K(self, Cs, nslices: int, Ks, stream=None):
+        nocc = (ctypes.c_int * len(Cs))(*[int(C.shape[1]) for C in Cs])
+        _check(lib().df_batch_build_K(self._h, _ptr_array(Cs), nocc, int(nslices), _ptr_array(Ks), _stream(stream)),
+               "df_batch_build_K")
+
+    def build_J(self, Ds, Js, stream=None):
+        _check(lib().df_batch_build_J(self._h, _ptr_array(Ds), _ptr_array(Js), _stream(stream)), "df_batch_build_J")
+
+    def autotune(self, Cs, nslices: int, Ks, stream=None):
+        nocc = (ctypes.c_int * len(Cs))(*[int(C.shape[1]) for C in Cs])
+        ch = (ctypes.c_int * 2)()
+        _check(lib().df_batch_autotune(self._h, _ptr_array(Cs), nocc, int(nslices), _ptr_array(Ks), _stream(stream),
+                                       ch), "df_batch_autotune")
+        return ch[0], ch[1]

@@ -149,6 +149,30 @@ def df_tensor(mol: Molecule) -> np.ndarray:
     return B
 
 
+def df_tensor_device(mol: Molecule, device="cuda"):
+    """B of Eq. cderi with the triangular solve on a CUDA device (torch / cuBLAS).
+
+    Input synthesis for the large workloads (batches, predictor training, the
+    240-atom molecule): the integrals and the metric's Cholesky factor are
+    formed on the host as in ``df_tensor``, the solve L B = (P|mu nu) runs on
+    the device.  The result agrees with ``df_tensor`` to the conditioning of
+    the metric, not bit for bit, so parity tests use ``df_tensor``.
+    Returns a contiguous float64 tensor [naux, nao, nao] on ``device``.
+    """
+    import scipy.linalg as sl
+    import torch
+    V = metric(mol)
+    L = torch.from_numpy(sl.cholesky(V, lower=True, check_finite=False)).to(device)
+    T = torch.from_numpy(int3c(mol).reshape(mol.naux, -1)).to(device)
+    B = torch.linalg.solve_triangular(L, T, upper=False)
+    del T
+    B = B.reshape(mol.naux, mol.nao, mol.nao).contiguous()
+    for p0 in range(0, mol.naux, 256):   # exact symmetry per P, in chunks
+        Bc = B[p0:p0 + 256]
+        Bc.copy_(0.5 * (Bc + Bc.transpose(1, 2)))
+    return B
+
+
 def orbitals(nao: int, nocc: int, seed: int) -> np.ndarray:
     """Orthonormal occupied coefficients C [nao, nocc] (QR of seeded N(0,1))."""
     rng = np.random.default_rng(seed)
