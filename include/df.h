@@ -178,6 +178,42 @@ df_status df_batch_build_J(df_batch *b, const double *const *D_dev, double *cons
 df_status df_batch_autotune(df_batch *b, const double *const *C_dev, const int *nocc, int nslices,
                             double *const *K_dev, void *stream, int *choice);
 
+/* ---- Learned slice-count predictor (per 128-function auxiliary block) ----
+ * A 16 -> 64 -> 64 -> 8 MLP (FP32, ReLU, softmax over slice counts 1..8)
+ * with hand-written CUDA forward, backward and Adam kernels.  Parameters are
+ * one float buffer of df_mlp_num_params() values: W1[64][16], b1[64],
+ * W2[64][64], b2[64], W3[8][64], b3[8] (y = W x + b).  The paper has no such
+ * part; it extends its closing suggestion (Section 5) of tying the emulation
+ * level to the change of the density matrix. */
+typedef struct df_mlp df_mlp;
+df_status df_mlp_create(df_mlp **out);  /* parameters zero; set them with df_mlp_set_params */
+void df_mlp_destroy(df_mlp *m);
+int df_mlp_num_params(void);
+df_status df_mlp_set_params(df_mlp *m, const float *host, int n);  /* also resets the Adam moments */
+df_status df_mlp_get_params(const df_mlp *m, float *host, int n);
+/* probs_dev [n][8] = softmax(MLP(X_dev [n][16])). */
+df_status df_mlp_forward(df_mlp *m, const float *X_dev, int n, float *probs_dev, void *stream);
+/* Gradient of the mean cross-entropy over (X_dev, y_dev in 0..7) into
+ * grad_host (df_mlp_num_params floats) and the loss into loss_host (either
+ * may be NULL; non-NULL synchronises). */
+df_status df_mlp_gradients(df_mlp *m, const float *X_dev, const int *y_dev, int n, float *grad_host,
+                           float *loss_host, void *stream);
+/* One Adam step (beta 0.9/0.999) on the mean cross-entropy. */
+df_status df_mlp_train_step(df_mlp *m, const float *X_dev, const int *y_dev, int n, float lr, float *loss_host,
+                            void *stream);
+/* 16 features per auxiliary block into F_dev [nblk][16]: block max and
+ * Frobenius norm of B, mean and spread of its row exponents, relative
+ * weight, small-row fraction (computed once from B), plus the iteration's
+ * log10 tolerance tau, ||D_k - D_{k-1}||_F, Delta E_rel and the rule's slice
+ * count. */
+df_status df_block_features(df_ctx *ctx, int nocc, double tau, double dD, double dE, int s_rule, float *F_dev,
+                            void *stream);
+/* Labels: err_host [nblk][8] = max |K_b(s) - K_b(FP64)| of every block at
+ * s = 1..8 (the emulated build against cuBLAS FP64, per block), *kmax_host =
+ * max|K(FP64)|.  Runs s_max + 1 builds; synchronises. */
+df_status df_block_errors(df_ctx *ctx, const double *C_dev, int nocc, double *err_host, double *kmax_host,
+                          void *stream);
+
 /* Phases timed when profiling is on (CUDA events on the call's stream). */
 #define DF_PHASE_SPLIT_C 0  /* C -> digit planes */
 #define DF_PHASE_GEMM1 1    /* X = B C on the tensor cores (or cuBLAS DGEMM in FP64 mode) */

@@ -348,6 +348,7 @@ void df_destroy(df_ctx *c) {
   cudaFree(c->E);
   cudaFree(c->sblk);
   cudaFree(c->status);
+  cudaFree(c->bstats);
   if (c->sblk_host) cudaFreeHost(c->sblk_host);
   for (int ph = 0; ph < DF_NPHASES; ++ph)
     for (auto &pr : c->ev[ph]) {

@@ -26,6 +26,7 @@ struct df_ctx {
   int *sblk = nullptr;      // device per-block slice counts
   int *sblk_host = nullptr; // pinned mirror of the last upload
   int *status = nullptr;
+  double *bstats = nullptr;  // static per-block statistics for the predictor's features
   int64_t bytes = 0;
   df_status last = DF_OK;
   cublasHandle_t cublas = nullptr;

@@ -78,6 +78,18 @@ def lib():
         L.df_batch_build_K.argtypes = [P, PP, ctypes.POINTER(ctypes.c_int), I, PP, V]
         L.df_batch_build_J.argtypes = [P, PP, PP, V]
         L.df_batch_autotune.argtypes = [P, PP, ctypes.POINTER(ctypes.c_int), I, PP, V, ctypes.POINTER(ctypes.c_int)]
+        FP = ctypes.POINTER(ctypes.c_float)
+        L.df_mlp_create.argtypes = [pp]
+        L.df_mlp_destroy.argtypes = [P]
+        L.df_mlp_destroy.restype = None
+        L.df_mlp_num_params.argtypes = []
+        L.df_mlp_set_params.argtypes = [P, FP, I]
+        L.df_mlp_get_params.argtypes = [P, FP, I]
+        L.df_mlp_forward.argtypes = [P, P, I, P, V]
+        L.df_mlp_gradients.argtypes = [P, P, P, I, FP, FP, V]
+        L.df_mlp_train_step.argtypes = [P, P, P, I, ctypes.c_float, FP, V]
+        L.df_block_features.argtypes = [P, I, D, D, D, I, P, V]
+        L.df_block_errors.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]
         L.df_workspace_bytes.argtypes = [P]
         L.df_workspace_bytes.restype = ctypes.c_int64
         _lib = L
@@ -283,3 +295,79 @@ class Batch:
         _check(lib().df_batch_autotune(self._h, _ptr_array(Cs), nocc, int(nslices), _ptr_array(Ks), _stream(stream),
                                        ch), "df_batch_autotune")
         return ch[0], ch[1]
+
+
+class MLP:
+    """The slice-count predictor network on the device (16 -> 64 -> 64 -> 8)."""
+
+    def __init__(self, params=None):
+        h = ctypes.c_void_p()
+        _check(lib().df_mlp_create(ctypes.byref(h)), "df_mlp_create")
+        self._h = h
+        self.n_params = lib().df_mlp_num_params()
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().df_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.n_params
+        _check(lib().df_mlp_set_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+               "df_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().df_mlp_get_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+               "df_mlp_get_params")
+        return a
+
+    def forward(self, X, stream=None):
+        assert X.dtype == torch.float32 and X.shape[1] == 16
+        probs = torch.empty((X.shape[0], 8), dtype=torch.float32, device=X.device)
+        _check(lib().df_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(probs), _stream(stream)), "df_mlp_forward")
+        return probs
+
+    def gradients(self, X, y, stream=None):
+        import numpy as np
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().df_mlp_gradients(self._h, _ptr(X), _ptr(y), X.shape[0],
+                                      g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss),
+                                      _stream(stream)), "df_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, X, y, lr, want_loss=False, stream=None):
+        loss = ctypes.c_float()
+        _check(lib().df_mlp_train_step(self._h, _ptr(X), _ptr(y), X.shape[0], float(lr),
+                                       ctypes.byref(loss) if want_loss else None, _stream(stream)),
+               "df_mlp_train_step")
+        return loss.value if want_loss else None
+
+
+def block_features(ctx, nocc, tau, dD, dE, s_rule, stream=None):
+    F = torch.empty((ctx.nblk, 16), dtype=torch.float32, device="cuda")
+    _check(lib().df_block_features(ctx._h, int(nocc), float(tau), float(dD), float(dE), int(s_rule), _ptr(F),
+                                   _stream(stream)), "df_block_features")
+    return F
+
+
+def block_errors(ctx, C, stream=None):
+    """(err [nblk, 8] max|K_b(s) - K_b(FP64)| for s = 1..8, max|K(FP64)|)."""
+    import numpy as np
+    err = np.zeros((ctx.nblk, 8))
+    kmax = ctypes.c_double()
+    _check(lib().df_block_errors(ctx._h, _f64(C), C.shape[1], err.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.byref(kmax), _stream(stream)), "df_block_errors")
+    return err, kmax.value
