@@ -44,7 +44,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["small", "profile", "medium", "large", "batch"], default="medium")
+    ap.add_argument("--workload", choices=["small", "profile", "medium", "large", "batch", "sequence", "predictor"],
+                    default="medium")
+    ap.add_argument("--size", choices=["small", "profile", "medium", "large"], default="medium",
+                    help="molecule of the sequence / predictor evaluation")
+    ap.add_argument("--train-molecules", type=int, default=48)
     ap.add_argument("--batch-size", type=int, default=48)
     ap.add_argument("--nslices", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -241,14 +245,98 @@ def run_batch(args):
             "clocks": clk.summary()}
 
 
+def _molecule_on_device(w, order=False):
+    import torch
+    from paper_2601_08077_gb300 import df, inputs, predictor
+    mol = inputs.molecule(w.n_atoms, w.seed)
+    B = inputs.df_tensor_device(mol)
+    C = inputs.orbitals(mol.nao, w.nocc, w.seed + 1)
+    ctx = df.Context(mol.nao, mol.naux, w.nocc)
+    ctx.setup(B, perm=predictor.magnitude_order(B) if order else None)
+    return ctx, B, C
+
+
+def run_sequence(args):
+    """The 15-iteration SCF-like sequence under the Table 1 rule, against an all-FP64 sequence."""
+    import torch
+    from paper_2601_08077_gb300 import build, sequence
+    build.build_all()
+    torch.cuda.set_device(0)
+    w = workload(args.size)
+    ctx, B, C = _molecule_on_device(w)
+    orbs = sequence.orbital_sequence(C, 15, w.seed)
+    sequence.run(ctx, orbs[:2])                     # warm-up
+    rule = sequence.run(ctx, orbs)
+    rule8 = sequence.run(ctx, orbs, level0_slices=8)
+    fp64 = sequence.run(ctx, orbs, mode="fp64")
+    t_rule = sum(r["ms"] for r in rule)
+    t_rule8 = sum(r["ms"] for r in rule8)
+    t_fp64 = sum(r["ms"] for r in fp64)
+    FK = flops_K(w) * len(orbs)
+    return {"metric": "adaptive-precision DF sequence (15 iterations, J + K + energies per iteration)",
+            "workload": w.name, "ms_total_rule": t_rule, "ms_total_fp64": t_fp64, "speedup": t_fp64 / t_rule,
+            "effective_tflops_rule": FK / (t_rule * 1e-3) / 1e12,
+            "level0_as_8_slices": {"ms_total": t_rule8, "speedup": t_fp64 / t_rule8,
+                                   "effective_tflops": FK / (t_rule8 * 1e-3) / 1e12,
+                                   "dE_vs_fp64_final": rule8[-1]["dE_vs_fp64"],
+                                   "max_dK_rel_final": rule8[-1]["max_dK_rel"]},
+            "levels": [r["level"] for r in rule], "slices": [r.get("slices") for r in rule],
+            "ms_per_iteration": [round(r["ms"], 3) for r in rule],
+            "max_dK_rel": [r["max_dK_rel"] for r in rule], "dE_vs_fp64": [r["dE_vs_fp64"] for r in rule],
+            "density_change": [r["dnorm"] for r in rule], "E_final": rule[-1]["E"], "E_fp64_final": fp64[-1]["E"]}
+
+
+def run_predictor(args):
+    """Learned per-block slice counts: trained on generated molecules (labels from the method
+    against FP64), evaluated along the SCF-like sequence against the Table 1 rule."""
+    import torch
+    from paper_2601_08077_gb300 import build, inputs, predictor, sequence
+    build.build_all()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    Fs, ys = [], []
+    for w in inputs.training_workloads(args.train_molecules):
+        ctx, B, C = _molecule_on_device(w, order=True)
+        F, y, _, _ = predictor.molecule_dataset(ctx, torch.from_numpy(C).cuda())
+        Fs.append(F)
+        ys.append(y)
+        del ctx, B
+    F = torch.cat(Fs)
+    y = torch.cat(ys)
+    t_data = time.perf_counter() - t0
+    p = predictor.SlicePredictor(seed=0)
+    t0 = time.perf_counter()
+    hist = p.fit(F, y, steps=3000, lr=3e-3, batch=512)
+    t_train = time.perf_counter() - t0
+    acc = float((p.mlp.forward(F).argmax(1).to(torch.int32) == y).float().mean())
+    w = workload(args.size)
+    ctx, B, C = _molecule_on_device(w, order=True)
+    orbs = sequence.orbital_sequence(C, 15, w.seed)
+    recs = sequence.run(ctx, orbs, mode="predictor", predictor=p, check_blocks=True)
+    rule = sequence.run(ctx, orbs)
+    wp = sum(r.get("work_pred", 0) for r in recs)
+    wr = sum(r.get("work_rule", 0) for r in recs)
+    wu = sum(r.get("work_uniform", 0) for r in recs)
+    return {"metric": "learned per-block slice counts vs the Table 1 rule", "train_molecules": args.train_molecules,
+            "train_samples": int(F.shape[0]), "train_seconds": t_train, "data_seconds": t_data,
+            "loss_first_last": [hist[0], hist[-1]], "train_accuracy": acc, "eval_workload": w.name,
+            "slice_pair_work": {"predictor": wp, "best_uniform_same_budget": wu, "rule_level_counts": wr},
+            "recomputed_blocks": sum(r.get("recomputed", 0) for r in recs),
+            "fallback_blocks": sum(r.get("fallbacks", 0) for r in recs),
+            "ms_predictor": sum(r["ms"] for r in recs), "ms_rule": sum(r["ms"] for r in rule),
+            "dE_vs_fp64_final": {"predictor": recs[-1]["dE_vs_fp64"], "rule": rule[-1]["dE_vs_fp64"]},
+            "levels": [r["level"] for r in recs]}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload == "batch":
+    if args.workload in ("batch", "sequence", "predictor"):
         if rank == 0:
-            print(json.dumps(run_batch(args)), flush=True)
+            fn = {"batch": run_batch, "sequence": run_sequence, "predictor": run_predictor}[args.workload]
+            print(json.dumps(fn(args)), flush=True)
         return
     w = workload(args.workload)
 

@@ -74,6 +74,15 @@ void df_destroy(df_ctx *ctx);
  * (Section 3.2).  B is constant over the SCF iterations, so this runs once. */
 df_status df_setup(df_ctx *ctx, const double *B_dev, void *stream);
 
+/* As df_setup, with the exchange path taking the auxiliary functions in the
+ * order perm_host[0..naux-1] (a permutation, new position -> original P):
+ * the 128-function blocks, their per-(block, mu) scales and per-block slice
+ * counts follow that order.  J and the final K are sums over all P and do
+ * not depend on it.  Ordering by magnitude (largest max|B_P| first) gives
+ * blocks of similar scale, which the per-block slice counts can exploit.
+ * NULL = the natural order.  DF_ERR_ARG if perm_host is not a permutation. */
+df_status df_setup_ordered(df_ctx *ctx, const double *B_dev, const int *perm_host, void *stream);
+
 /* Coulomb build in FP64 (Eqs. df-j-1, df-j-2; the paper keeps J in FP64,
  * Section 3.1).  D_dev symmetric [nao][nao]; J_dev [nao][nao] out;
  * rho_dev [naux] out (may be NULL: then an internal buffer is used). */
@@ -145,6 +154,10 @@ int df_level_slices(int level);
  * >= 0, any level <= it is run as native FP64 (the hardware-specific
  * fallback of Section 3.2). */
 df_status df_adaptive_reset(df_ctx *ctx, int fp64_from_level);
+/* Slice count run at level 0 (the paper's FP64 level): 0 (default) = native
+ * FP64; 7 or 8 = emulation at that many slices (a GB300 variant: its FP64
+ * rate is ~40x below the 8-slice emulation, whose K error is ~2e-15). */
+df_status df_adaptive_level0(df_ctx *ctx, int nslices);
 df_status df_adaptive_next(df_ctx *ctx, double energy, int *level_out, int *nslices_out);
 
 /* Read (and clear) the device status word; synchronises `stream`. */

@@ -349,6 +349,7 @@ void df_destroy(df_ctx *c) {
   cudaFree(c->sblk);
   cudaFree(c->status);
   cudaFree(c->bstats);
+  cudaFree(c->perm);
   if (c->sblk_host) cudaFreeHost(c->sblk_host);
   for (int ph = 0; ph < DF_NPHASES; ++ph)
     for (auto &pr : c->ev[ph]) {
@@ -390,13 +391,31 @@ df_status df_phase_times(df_ctx *c, double *ms, int *count) {
 
 df_status df_last_error(const df_ctx *c) { return c ? c->last : DF_ERR_ARG; }
 
-df_status df_setup(df_ctx *c, const double *B_dev, void *stream) {
+df_status df_setup(df_ctx *c, const double *B_dev, void *stream) { return df_setup_ordered(c, B_dev, nullptr, stream); }
+
+df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host, void *stream) {
   if (!c || !B_dev) return record(c, DF_ERR_ARG);
   cudaStream_t st = as_stream(stream);
   c->B = B_dev;
+  if (perm_host) {
+    std::vector<char> seen(c->naux, 0);
+    for (int i = 0; i < c->naux; ++i) {
+      if (perm_host[i] < 0 || perm_host[i] >= c->naux || seen[perm_host[i]]) return record(c, DF_ERR_ARG);
+      seen[perm_host[i]] = 1;
+    }
+    if (!c->perm) DF_TRY(c, cudaMalloc(&c->perm, sizeof(int) * c->naux));
+    DF_TRY(c, cudaMemcpy(c->perm, perm_host, sizeof(int) * c->naux, cudaMemcpyHostToDevice));
+  } else if (c->perm) {
+    cudaFree(c->perm);
+    c->perm = nullptr;
+  }
+  if (c->bstats) {
+    cudaFree(c->bstats);
+    c->bstats = nullptr;
+  }
   const long long rows = (long long)c->naux * c->nao;
   DF_TRY(c, df::launch_split_rows_bf16(B_dev, rows, c->nao, c->nao, c->s_max, c->eB, c->Bd, c->ld_nao,
-                                       rows * c->ld_nao, st));
+                                       rows * c->ld_nao, st, c->perm, c->nao));
   c->ready = true;
   return DF_OK;
 }
@@ -470,6 +489,12 @@ df_status df_adaptive_reset(df_ctx *c, int fp64_from_level) {
   return DF_OK;
 }
 
+df_status df_adaptive_level0(df_ctx *c, int nslices) {
+  if (!c || nslices < 0 || nslices > c->s_max) return DF_ERR_ARG;
+  c->level0_slices = nslices;
+  return DF_OK;
+}
+
 df_status df_adaptive_next(df_ctx *c, double energy, int *level_out, int *nslices_out) {
   if (!c || !level_out || !nslices_out) return DF_ERR_ARG;
   if (c->iter > 0 && energy != 0.0) {
@@ -480,8 +505,8 @@ df_status df_adaptive_next(df_ctx *c, double energy, int *level_out, int *nslice
   c->E_prev = energy;
   c->iter += 1;
   *level_out = c->level;
-  const bool fp64 = c->level == 0 || (c->fp64_from >= 0 && c->level <= c->fp64_from);
-  *nslices_out = fp64 ? 0 : df_level_slices(c->level);
+  const bool fp64 = (c->level == 0 && c->level0_slices == 0) || (c->fp64_from >= 0 && c->level <= c->fp64_from);
+  *nslices_out = fp64 ? 0 : (c->level == 0 ? c->level0_slices : df_level_slices(c->level));
   return DF_OK;
 }
 

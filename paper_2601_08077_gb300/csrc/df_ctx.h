@@ -27,6 +27,7 @@ struct df_ctx {
   int *sblk_host = nullptr; // pinned mirror of the last upload
   int *status = nullptr;
   double *bstats = nullptr;  // static per-block statistics for the predictor's features
+  int *perm = nullptr;       // exchange-path order of the auxiliary functions (P' -> P), or null
   int64_t bytes = 0;
   df_status last = DF_OK;
   cublasHandle_t cublas = nullptr;
@@ -35,7 +36,7 @@ struct df_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[DF_NPHASES];
   std::vector<cudaEvent_t> pool;
   // adaptive controller (Section 3.2)
-  int level = 4, iter = 0, fp64_from = -1;
+  int level = 4, iter = 0, fp64_from = -1, level0_slices = 0;
   double E_prev = 0.0;
 };
 

@@ -69,7 +69,7 @@ struct Ctx;
 // Kernel launchers (split.cu, slicegemm.cu, coulomb.cu).
 cudaError_t launch_split_rows_bf16(const double *A, long long rows, int cols, long long ld, int nslices,
                                    int *exps, uint16_t *digits, long long dld, long long plane_stride,
-                                   cudaStream_t st);
+                                   cudaStream_t st, const int *perm = nullptr, int group = 1);
 cudaError_t launch_split_rows_int8(const double *A, int rows, int cols, int ld, int nslices, int *exps,
                                    int8_t *digits, cudaStream_t st);
 cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int nslices, int *exps,

@@ -153,23 +153,27 @@ __global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ G, 
 // exponents over nonzero rows, [3] nonzero rows, [4] min exponent, [5] max
 // exponent, [6] rows with exponent < max_e - 20 (filled in a second pass).
 __global__ void __launch_bounds__(256) block_stats_kernel(const double *__restrict__ B, const int *__restrict__ eB,
-                                                          int naux, int nao, double *__restrict__ stats) {
+                                                          const int *__restrict__ perm, int naux, int nao,
+                                                          double *__restrict__ stats) {
   const int b = blockIdx.x;
   const int p0 = b * df::kBlock;
   const int nP = min(df::kBlock, naux - p0);
-  const long long n = (long long)nP * nao * nao;
-  const double *src = B + (long long)p0 * nao * nao;
+  const long long n2 = (long long)nao * nao;
   double mx = 0.0, ss = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const double v = src[i];
-    mx = fmax(mx, fabs(v));
-    ss = fma(v, v, ss);
+  for (int pl = 0; pl < nP; ++pl) {
+    const int P = perm ? perm[p0 + pl] : p0 + pl;
+    const double *src = B + (long long)P * n2;
+    for (long long i = threadIdx.x; i < n2; i += blockDim.x) {
+      const double v = src[i];
+      mx = fmax(mx, fabs(v));
+      ss = fma(v, v, ss);
+    }
   }
   double esum = 0.0, cnt = 0.0, emin = 1e9, emax = -1e9;
   const int rows = nP * nao;
   for (int r = threadIdx.x; r < rows; r += blockDim.x) {
     const int e = eB[(long long)p0 * nao + r];
-    // a zero row has exponent 0 and contributes nothing: count rows whose max is nonzero
+    // every row of the block counts (a zero row has exponent 0)
     esum += e;
     cnt += 1.0;
     emin = fmin(emin, (double)e);
@@ -364,7 +368,7 @@ df_status df_block_features(df_ctx *c, int nocc, double tau, double dD, double d
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (!c->bstats) {
     if (cudaMalloc(&c->bstats, sizeof(double) * 8 * c->nblk) != cudaSuccess) return DF_ERR_OOM;
-    block_stats_kernel<<<c->nblk, 256, 0, st>>>(c->B, c->eB, c->naux, c->nao, c->bstats);
+    block_stats_kernel<<<c->nblk, 256, 0, st>>>(c->B, c->eB, c->perm, c->naux, c->nao, c->bstats);
     if (cudaGetLastError() != cudaSuccess) return DF_ERR_CUDA;
   }
   block_features_kernel<<<(c->nblk + 127) / 128, 128, 0, st>>>(c->bstats, c->nblk, c->naux, c->nao, nocc, tau, dD,

@@ -34,11 +34,14 @@ __global__ void __launch_bounds__(256) split_rows_bf16_kernel(const double *__re
                                                               int cols, long long ld, int nslices,
                                                               int *__restrict__ exps,
                                                               uint16_t *__restrict__ digits, long long dld,
-                                                              long long plane_stride, int vec2) {
+                                                              long long plane_stride, int vec2,
+                                                              const int *__restrict__ perm, int group) {
   const int lane = threadIdx.x & 31;
   const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= rows) return;
-  const double *row = A + r * ld;
+  // with a permutation, output row r = (P', j) reads input row (perm[P'], j), `group` rows per P
+  const long long src = perm ? (long long)perm[r / group] * group + (r % group) : r;
+  const double *row = A + src * ld;
   uint64_t m = 0;
   if (vec2) {
     const double2 *row2 = reinterpret_cast<const double2 *>(row);
@@ -257,13 +260,13 @@ __global__ void kpart_reduce_kernel(const long long *__restrict__ Rp, const int 
 
 cudaError_t launch_split_rows_bf16(const double *A, long long rows, int cols, long long ld, int nslices,
                                    int *exps, uint16_t *digits, long long dld, long long plane_stride,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, const int *perm, int group) {
   if (rows <= 0) return cudaSuccess;
   const int vec2 = ((ld & 1) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) ? 1 : 0;
   const int wpb = 8;
   dim3 grid((unsigned)((rows + wpb - 1) / wpb));
   split_rows_bf16_kernel<<<grid, 32 * wpb, 0, st>>>(A, rows, cols, ld, nslices, exps, digits, dld,
-                                                    plane_stride, vec2);
+                                                    plane_stride, vec2, perm, group > 0 ? group : 1);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ def lib():
         L.df_destroy.argtypes = [P]
         L.df_destroy.restype = None
         L.df_setup.argtypes = [P, P, V]
+        L.df_setup_ordered.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), V]
         L.df_build_J.argtypes = [P, P, P, P, V]
         L.df_build_K.argtypes = [P, P, I, I, P, ctypes.POINTER(KStats), V]
         L.df_build_K_blocks.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(KStats), V]
@@ -63,6 +64,7 @@ def lib():
         L.df_level_slices.argtypes = [I]
         L.df_level_slices.restype = I
         L.df_adaptive_reset.argtypes = [P, I]
+        L.df_adaptive_level0.argtypes = [P, I]
         L.df_adaptive_next.argtypes = [P, D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.df_sync_status.argtypes = [P, V]
         L.df_last_error.argtypes = [P]
@@ -189,10 +191,15 @@ class Context:
     def workspace_bytes(self) -> int:
         return int(lib().df_workspace_bytes(self._h))
 
-    def setup(self, B: torch.Tensor, stream=None):
+    def setup(self, B: torch.Tensor, perm=None, stream=None):
+        """Attach B; `perm` (new position -> original P) orders the exchange path's auxiliary functions."""
         assert B.shape == (self.naux, self.nao, self.nao)
         self._B = B  # the library keeps the pointer: keep the tensor alive
-        _check(lib().df_setup(self._h, _f64(B), _stream(stream)), "df_setup")
+        if perm is None:
+            _check(lib().df_setup(self._h, _f64(B), _stream(stream)), "df_setup")
+        else:
+            arr = (ctypes.c_int * self.naux)(*[int(x) for x in perm])
+            _check(lib().df_setup_ordered(self._h, _f64(B), arr, _stream(stream)), "df_setup_ordered")
 
     def build_J(self, D, J=None, rho=None, stream=None):
         if J is None:
@@ -229,6 +236,9 @@ class Context:
 
     def adaptive_reset(self, fp64_from_level: int = -1):
         _check(lib().df_adaptive_reset(self._h, int(fp64_from_level)), "df_adaptive_reset")
+
+    def adaptive_level0(self, nslices: int):
+        _check(lib().df_adaptive_level0(self._h, int(nslices)), "df_adaptive_level0")
 
     def adaptive_next(self, energy: float):
         lv, ns = ctypes.c_int(), ctypes.c_int()

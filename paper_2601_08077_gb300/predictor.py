@@ -53,6 +53,11 @@ def init_params(seed: int) -> np.ndarray:
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 
+def magnitude_order(B: torch.Tensor) -> np.ndarray:
+    """Auxiliary functions by decreasing max|B_P| (for df_setup_ordered): blocks of similar scale."""
+    return torch.argsort(B.abs().amax(dim=(1, 2)), descending=True).cpu().numpy()
+
+
 def molecule_dataset(ctx, C, taus=TAUS, dD=1e-3, dE=1e-6):
     """Features and labels of every block of one molecule at every tolerance."""
     err, kmax = df.block_errors(ctx, C)
