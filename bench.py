@@ -297,7 +297,7 @@ def run_predictor(args):
     Fs, ys = [], []
     for w in inputs.training_workloads(args.train_molecules):
         ctx, B, C = _molecule_on_device(w, order=True)
-        F, y, _, _ = predictor.molecule_dataset(ctx, torch.from_numpy(C).cuda())
+        F, y, _, _ = predictor.molecule_dataset(ctx, torch.from_numpy(C).cuda(), seed=w.seed)
         Fs.append(F)
         ys.append(y)
         del ctx, B

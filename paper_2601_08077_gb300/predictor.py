@@ -17,7 +17,7 @@ import torch
 from . import df
 
 # Table 1's printed accuracies (levels 4..1) and the 1e-10 target of the K error
-TAUS = (1.2e-7, 4.7e-10, 1e-10, 1.8e-12)
+TAUS = (1.2e-7, 4.7e-10, 1e-10, 1.8e-12, 7.1e-15)
 
 
 def rule_slices(tau: float) -> int:
@@ -58,11 +58,18 @@ def magnitude_order(B: torch.Tensor) -> np.ndarray:
     return torch.argsort(B.abs().amax(dim=(1, 2)), descending=True).cpu().numpy()
 
 
-def molecule_dataset(ctx, C, taus=TAUS, dD=1e-3, dE=1e-6):
-    """Features and labels of every block of one molecule at every tolerance."""
+def molecule_dataset(ctx, C, taus=TAUS, seed=0):
+    """Features and labels of every block of one molecule at every tolerance.
+
+    The density-change and energy-change features are drawn log-uniformly over
+    the range an SCF-like sequence visits (the labels do not depend on them).
+    """
+    rng = np.random.default_rng(seed)
     err, kmax = df.block_errors(ctx, C)
     Fs, ys = [], []
     for tau in taus:
+        dD = 10.0 ** rng.uniform(-14, 0)
+        dE = 10.0 ** rng.uniform(-16, -2)
         Fs.append(df.block_features(ctx, C.shape[1], tau, dD, dE, rule_slices(tau)))
         ys.append(torch.from_numpy(labels_from_errors(err, kmax, tau) - 1).to(torch.int32).cuda())
     return torch.cat(Fs), torch.cat(ys), err, kmax
