@@ -149,6 +149,28 @@ def df_tensor(mol: Molecule) -> np.ndarray:
     return B
 
 
+def df_tensor_rows(mol: Molecule, nrows: int) -> np.ndarray:
+    """The first nrows auxiliary rows of B (Eq. cderi), without forming the rest.
+
+    Forward substitution makes row P of L^{-1} T depend only on rows <= P, and
+    the leading block of the Cholesky factor is the factor of the leading block
+    of the metric, so B[:nrows] needs only the first nrows auxiliary functions.
+    Equal to df_tensor(mol)[:nrows] up to the solver's rounding.
+    """
+    import scipy.linalg as sl
+    from scipy.linalg.blas import dtrsm
+    nrows = min(nrows, mol.naux)
+    sub = Molecule(mol.n_atoms, mol.seed, mol.edge, mol.xyz, mol.ao_xyz, mol.ao_exp,
+                   np.ascontiguousarray(mol.aux_xyz[:nrows]), np.ascontiguousarray(mol.aux_exp[:nrows]))
+    L = sl.cholesky(metric(sub), lower=True, check_finite=False)
+    T = int3c(sub).reshape(nrows, -1)
+    Bt = dtrsm(1.0, L, T.T, side=1, lower=1, trans_a=1, overwrite_b=1)
+    B = np.ascontiguousarray(Bt.T).reshape(nrows, mol.nao, mol.nao)
+    for P in range(nrows):
+        B[P] = 0.5 * (B[P] + B[P].T)
+    return B
+
+
 def df_tensor_device(mol: Molecule, device="cuda"):
     """B of Eq. cderi with the triangular solve on a CUDA device (torch / cuBLAS).
 

@@ -345,3 +345,13 @@ def test_flop_model():
         assert O.flops_K(nscr, nbf, naux, nocc) == 2 * nscr * naux * nocc + 2 * nbf * nbf * naux * nocc
         # K needs at least N_occ times the FLOPs of J because N_scr <= N_bf^2
         assert O.flops_K(nscr, nbf, naux, nocc) >= nocc * O.flops_J(nscr, naux)
+
+
+def test_df_tensor_rows_is_the_leading_block(small):
+    """Rows of B depend only on the leading auxiliary functions (forward substitution);
+    two triangular solves agree within n u cond(L) |B|."""
+    mol, B, _, _ = small
+    Bk = inputs.df_tensor_rows(mol, 128)
+    V = inputs.metric(mol)
+    tol = V.shape[0] * 2.0 ** -52 * math.sqrt(np.linalg.cond(V)) * np.max(np.abs(B))
+    assert np.max(np.abs(Bk - B[:128])) <= tol
