@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch-size", type=int, default=48)
     ap.add_argument("--nslices", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cluster-pairs", type=int, choices=[0, 1, 2], default=0,
+                    help="slice GEMMs on CTA pairs (cta_group::2): 0 never, 1 where every pair is useful, 2 always")
     return ap.parse_args()
 
 
@@ -376,6 +378,7 @@ def main():
     B = Bg
     ctx = df.Context(w.nao, w.naux, w.nocc)
     ctx.setup(Bg)
+    ctx.set_cluster_pairs(args.cluster_pairs)
     J = torch.empty((w.nao, w.nao), dtype=torch.float64, device=dev)
     K = torch.empty_like(J)
     rho = torch.empty(w.naux, dtype=torch.float64, device=dev)
@@ -487,6 +490,7 @@ def main():
         "data": "synthetic (seeded s-type Gaussian molecule, integrals and DF tensor generated)",
         "config": {"workload": w.name, "nao": w.nao, "naux": w.naux, "nocc": w.nocc, "nslices": s,
                    "level": 2, "l2": "inputs larger than L2 (B %.1f GB)" % (B_bytes / 1e9),
+                   "cluster_pairs": args.cluster_pairs,
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": FK / (ms_e2e * 1e-3) / 1e12 * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},

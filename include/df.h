@@ -248,6 +248,22 @@ df_status df_phase_times(df_ctx *ctx, double *ms, int *count);
 /* Device bytes held by the context's workspaces. */
 int64_t df_workspace_bytes(const df_ctx *ctx);
 
+/* Execution options of a context (they change speed, never results: every
+ * option gives bit-identical K).
+ *
+ * DF_OPT_CLUSTER_PAIRS — whether the two slice GEMMs of df_build_K /
+ * df_build_K_blocks (Section 3.2's slice products) run on CTA pairs: a
+ * cluster of two CTAs whose M = 256 tcgen05 MMA (cta_group::2) covers two
+ * output tiles that share the stacked B operand, each CTA staging its own A
+ * tile and half of B.  0 never (default: on GB300 it measured no faster than
+ * one CTA per tile), 1 where every pair is useful (the first GEMM whenever
+ * its occupied-orbital tiles pair up, the second from six AO tiles on), 2
+ * wherever the layout pairs.
+ *
+ * Returns DF_ERR_ARG for an unknown option or value; the context is unchanged. */
+#define DF_OPT_CLUSTER_PAIRS 1
+df_status df_set_option(df_ctx *ctx, int option, int value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -157,6 +157,7 @@ bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap 
   p.out = c->X;
   p.out_ld = nocc;
   p.status = c->status;
+  p.pair = c->pair_mode;
   return true;
 }
 
@@ -185,6 +186,7 @@ bool gemm2_setup(df_ctx *c, int nocc, int nsplit, SgParams &q2, CUtensorMap &tx)
   q2.out_ld = nao;
   q2.out_blk = (long long)nao * nao;
   q2.status = c->status;
+  q2.pair = c->pair_mode;
   return true;
 }
 
@@ -367,6 +369,17 @@ df_status df_set_profiling(df_ctx *c, int on) {
   if (!c) return DF_ERR_ARG;
   c->profiling = on != 0;
   return DF_OK;
+}
+
+df_status df_set_option(df_ctx *c, int option, int value) {
+  if (!c) return DF_ERR_ARG;
+  switch (option) {
+    case DF_OPT_CLUSTER_PAIRS:
+      if (value < 0 || value > 2) return DF_ERR_ARG;
+      c->pair_mode = value;
+      return DF_OK;
+  }
+  return DF_ERR_ARG;
 }
 
 df_status df_phase_times(df_ctx *c, double *ms, int *count) {

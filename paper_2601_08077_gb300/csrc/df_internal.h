@@ -50,7 +50,17 @@ struct SgParams {
   double *out;
   long long *raw;
   int *status;              // device status word (DF_ERR_TIMEOUT bits)
+  // CTA-pair mode: two CTAs of a cluster take two tiles that share their
+  // B-side operand, which each loads half of and multicasts to both.
+  // Work is then counted in tile pairs (npairs); the host sets both.
+  int pair;
+  int npairs;
 };
+
+// Tile pairs of a launch in CTA-pair mode (0 = the layout has no pairing):
+// kLayoutGrid / kLayoutX pair m tiles 2a, 2a+1 of one n tile (nt_m even);
+// kLayoutKPart pairs m tiles 2a, 2a+1 of n tile j >= 2a per (block, split).
+long long slice_gemm_pairs(const SgParams &p);
 
 // A grouped launch: the work units of several problems (molecules) in one
 // persistent launch.  Problem i owns units [unit_off[i], unit_off[i+1]); its

@@ -14,21 +14,29 @@
 // through tcgen05.mma .kind::f16 with FP32 accumulators in TMEM.  A product of
 // two digits is at most 2^14 in magnitude, so an accumulation of at most 1024
 // products stays within 2^24 and is exact in FP32; the MMA warp therefore
-// closes an accumulator "chunk" every 1024 products (16 pipeline stages) and
-// the epilogue warps add it exactly into an int32 sum of the group held in
-// registers (one convert and one integer add per element per chunk).  At the
-// end of a group (or every 64 chunks, before the int32 sum could overflow)
-// the group sum is folded, shifted by its group's weight, into an int64
-// fixed-point total kept in TMEM.  TMEM columns 0-255 hold two FP32
-// accumulator buffers (the tensor core fills one while the epilogue drains
-// the other), columns 256-511 the int64 totals (two 32-bit columns each).
+// closes an accumulator "chunk" every <= 1024 products (<= 16 pipeline
+// stages) and the epilogue warps add it, converted to integers and shifted by
+// its group's weight, into an int64 fixed-point total held in registers (64
+// per thread).  One tcgen05.mma (M = 128, N = 256) computes two slice pairs
+// (t, u) and (t, u+1) at once: its B operand is B_u stacked on B_{u+1}, so
+// TMEM columns 0-255 hold one accumulator buffer of 2 x 128 columns and
+// columns 256-511 the second (the tensor core fills one while the epilogue
+// drains the other).
 //
-// Warp roles (320 threads, one CTA per SM, persistent over work units):
-//   warp 0      TMA producer: 128x64 BF16 boxes of A_t and B_u, 128B swizzle,
-//               into a 6-stage ring (32 KB per stage) guarded by mbarriers;
+// Warp roles (384 threads, one CTA per SM, persistent over work units):
+//   warp 0      TMA producer: 128x64 BF16 boxes of A_t, B_u and B_{u+1},
+//               128B swizzle, into a 4-stage ring (48 KB per stage) guarded
+//               by mbarriers;
 //   warp 1      TMEM allocation and the single-thread tcgen05.mma issuer;
-//   warps 2..9  epilogue; warp w reads TMEM lanes 32*(w%4)..+31 (tile rows)
-//               and columns 64*((w-2)/4)..+63.
+//   warps 2, 3  idle (they give their registers to the epilogue: setmaxnreg);
+//   warps 4..11 epilogue; warp w reads TMEM lanes 32*(w%4)..+31 (tile rows)
+//               and columns 64*((w-4)/4)..+63 of each 128-column half.
+//
+// CTA-pair mode (cluster of two): rank 0's MMA issuer runs tcgen05.mma
+// .cta_group::2 with M = 256 over two output tiles that share the B operand;
+// each CTA stages its own A tile and one of the two stacked B tiles (a
+// 6-stage ring of 32 KB), both CTAs' copies complete on rank 0's barriers,
+// the commits arrive on both CTAs' barriers, and each CTA drains its own TMEM.
 //
 // Every mbarrier wait is bounded (4 s of wall clock); a wait that runs out
 // sets a shared abort flag and bit 1 of the device status word, every role
@@ -46,6 +54,10 @@ namespace {
 constexpr int kStages = 4;
 constexpr int kTileBytes = kTile * kKTile * 2;        // one 128 x 64 BF16 box, 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;           // A_t tile + two stacked B tiles
+// CTA-pair mode (cta_group::2): a CTA stages its own A_t tile and one of the
+// two stacked B tiles, so a stage is 32 KB and six fit in the same space.
+constexpr int kStagesP = 6;
+constexpr int kStageBytesP = 2 * kTileBytes;
 constexpr int kThreads = 384;                         // 12 warps
 constexpr int kEpiWarp0 = 4;
 constexpr int kEpiWarps = 8;
@@ -68,6 +80,11 @@ constexpr uint32_t idesc_for(int n) {
 }
 constexpr uint32_t kIdesc128 = idesc_for(128);
 constexpr uint32_t kIdesc256 = idesc_for(256);
+// M = 256 across the CTA pair (128 rows of A in each CTA), N = 256 (B rows
+// 0-127 from the first CTA's shared memory, 128-255 from the second's).
+constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
+                                ((uint32_t)(256 >> 4) << 24);
+static_assert(kStagesP * kStageBytesP <= kStages * kStageBytes, "pair ring must fit the same shared memory");
 
 struct Unit {
   int m0, n0, az0, azs, bz0, bzs, kt0, ktiles, s, blk, part;
@@ -102,13 +119,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Acquire at cluster scope: the barrier may complete through arrivals or
+// copies issued by the other CTA of a pair.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait.  Returns false if the CTA is aborting or the wait ran out.
+template <bool kCluster = false>
 __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                              int *status, bool honour_abort = true) {
-  if (mbar_try_wait(bar, parity)) return true;
+  auto poll = [&]() { return kCluster ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
+  if (poll()) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (poll()) return true;
     if (honour_abort && *abort_flag) return false;
     if (globaltimer_ns() - t0 > kTimeoutNs) {
       *abort_flag = 1;
@@ -155,6 +188,61 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// --- CTA pair (cta_group::2) ---------------------------------------------
+// TMA load into this CTA's shared memory that completes its bytes on the
+// mbarrier at shared::cluster address `mbar` (rank 0's, for both CTAs).
+__device__ __forceinline__ void tma_load_3d_pair(void *dst, const CUtensorMap *map, uint32_t mbar, int c0, int c1,
+                                                 int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+      : "memory");
+}
+
+// One thread of the first CTA issues the M = 256 MMA for both CTAs.
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive (once the pair's MMAs issued so far are done) on the barrier at the
+// same offset in both CTAs of the pair.
+__device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
+// Shared::cluster address of this CTA's variable `p` in CTA `rank`.
+__device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Every thread of both CTAs of the cluster.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -174,33 +262,39 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Tile (i, j) of block-and-split index bs of the second exchange GEMM.
+__device__ __forceinline__ Unit kpart_unit(const SgParams &p, int i, int j, int bs) {
+  Unit w;
+  const int b = bs / p.nsplit;
+  const int sp = bs - b * p.nsplit;
+  w.m0 = i * kTile;
+  w.n0 = j * kTile;
+  w.az0 = b;
+  w.azs = p.nblk;
+  w.bz0 = b;
+  w.bzs = p.nblk;
+  const int nP = min(kBlock, p.naux - b * kBlock);
+  const int kt_b = (nP * p.nocc + kKTile - 1) / kKTile;
+  w.kt0 = (int)((long long)kt_b * sp / p.nsplit);
+  w.ktiles = (int)((long long)kt_b * (sp + 1) / p.nsplit) - w.kt0;
+  w.s = p.s_blk[b];
+  w.blk = b;
+  w.part = bs;
+  return w;
+}
+
 __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
   Unit w;
   if (p.layout == kLayoutKPart) {
     // u -> (block b, K split sp, upper tile pair); block-major for L2 reuse
     const int npairs = p.nt_m * (p.nt_m + 1) / 2;
     const int pr = u % npairs;
-    const int bs = u / npairs;
-    const int b = bs / p.nsplit;
-    const int sp = bs - b * p.nsplit;
     int i = 0, rem = pr;
     while (rem >= p.nt_m - i) {
       rem -= p.nt_m - i;
       ++i;
     }
-    w.m0 = i * kTile;
-    w.n0 = (i + rem) * kTile;
-    w.az0 = b;
-    w.azs = p.nblk;
-    w.bz0 = b;
-    w.bzs = p.nblk;
-    const int nP = min(kBlock, p.naux - b * kBlock);
-    const int kt_b = (nP * p.nocc + kKTile - 1) / kKTile;
-    w.kt0 = (int)((long long)kt_b * sp / p.nsplit);
-    w.ktiles = (int)((long long)kt_b * (sp + 1) / p.nsplit) - w.kt0;
-    w.s = p.s_blk[b];
-    w.blk = b;
-    w.part = bs;
+    return kpart_unit(p, i, i + rem, u / npairs);
   } else {
     const int mt = u % p.nt_m;
     const int nt = u / p.nt_m;
@@ -224,6 +318,29 @@ __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
   return w;
 }
 
+// Tile of CTA `r` (0 or 1) of tile pair `pu` in CTA-pair mode: both tiles
+// share the n tile (the B-side operand), their m tiles are 2a and 2a+1.  In
+// the second exchange GEMM the pairs of (block, split) bs are (2a + r, j) for
+// j = 2a .. nt-1: the pair at j = 2a also computes the lower tile (2a+1, 2a),
+// whose values are the transpose of an upper tile and are never read, and an
+// m tile past the last one reads zeros and stores nothing.
+__device__ __forceinline__ Unit decode_pair(const SgParams &p, int pu, int r) {
+  if (p.layout == kLayoutKPart) {
+    const int nt = p.nt_m;
+    const int na = (nt + 1) / 2;
+    const int per = na * (nt - na + 1);  // sum over a < na of (nt - 2a)
+    const int pr = pu % per;
+    int a = 0, rem = pr;
+    while (rem >= nt - 2 * a) {
+      rem -= nt - 2 * a;
+      ++a;
+    }
+    return kpart_unit(p, 2 * a + r, 2 * a + rem, pu / per);
+  }
+  const int h = p.nt_m >> 1;
+  return decode_unit(p, 2 * (pu % h) + r + p.nt_m * (pu / h));
+}
+
 // Epilogue store of the 64 output columns n0c..n0c+63 of row m.
 template <int kMode>
 __device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m, int n0c, const long long (&R)[64],
@@ -243,6 +360,11 @@ __device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m,
   }
 }
 
+// K tiles of a unit are taken in ceil(ktiles / 16) chunks of near-equal
+// length (at most 16 stages = 1024 products each, the exact FP32 range).
+__device__ __forceinline__ int num_chunks(int ktiles) { return (ktiles + kChunkStages - 1) / kChunkStages; }
+__device__ __forceinline__ int chunk_begin(int ktiles, int nch, int c) { return ktiles * c / nch; }
+
 __device__ __forceinline__ long long weigh(int v, int sh) {
   const long long x = (long long)v;
   return sh >= 0 ? (x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
@@ -251,8 +373,11 @@ __device__ __forceinline__ long long weigh(int v, int sh) {
 // The work of one unit is a sequence of "slots": for t = 0..s-1, u0 = 0, 2, 4, ...
 // <= s-1-t, the slot computes the slice pairs (t, u0) and, if u0+1 <= s-1-t,
 // (t, u0+1) with one N = 256 MMA per K step (B operand = B_u0 stacked on
-// B_u0+1); a single pair uses N = 128.  Each slot runs over all K tiles of
-// the unit in chunks of at most 16 stages (1024 products per accumulator).
+// B_u0+1); a single pair uses N = 128.  The K tiles of the unit are cut into
+// chunks of at most 16 stages (1024 products per accumulator); the chunk loop
+// is the outer one, so every slot of a chunk reads the same few K tiles of
+// all slices while they are still in L2 (the int64 total is a plain sum, so
+// the order of the chunk drains does not change it).
 // Parameters and operand maps of global unit u: the launch's own (single
 // problem) or, in a grouped launch, those of the problem that owns u.
 template <bool kGrouped>
@@ -276,45 +401,65 @@ __device__ __forceinline__ const SgParams &unit_params(const SgParams &p, const 
   return g.params[lo];
 }
 
-template <int kMode, bool kGrouped>
+template <int kMode, bool kGrouped, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
                       const SgParams p, const SgGroup grp) {
+  constexpr int NS = kPair ? kStagesP : kStages;
+  constexpr int SB = kPair ? kStageBytesP : kStageBytes;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
-  uint64_t *empty = full + kStages;
-  uint64_t *acc_full = empty + kStages;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + NS * SB);
+  uint64_t *empty = full + NS;
+  uint64_t *acc_full = empty + NS;
   uint64_t *acc_empty = acc_full + kAccBufs;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + kAccBufs);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // CTA pair: rank 0 issues the MMAs of both CTAs; each CTA loads its own A
+  // tile and B tile, drains its own TMEM rows and writes its own output tile.
+  const int crank = kPair ? (int)cluster_ctarank() : 0;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < NS; ++i) {
+      // pair: rank 0's full barriers count the bytes of both CTAs' copies
+      // (rank 0's producer expects them all); rank 1's are not used
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < kAccBufs; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], kEpiWarps);
+      mbar_init(&acc_empty[i], kPair ? 2 * kEpiWarps : kEpiWarps);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (kPair) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
   __syncthreads();
+  // the other CTA's arrivals and commits may target this CTA's barriers from now on
+  if (kPair) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int total_units = kGrouped ? grp.total : p.nunits;
+  const int total_units = kGrouped ? grp.total : (kPair ? p.npairs : p.nunits);
+  const int first_unit = kPair ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int unit_stride = kPair ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -322,90 +467,133 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+      const uint32_t full0 = kPair ? peer_addr(full, 0) : 0u;
+      for (int u = first_unit; u < total_units && ok; u += unit_stride) {
         int lu, mol;
         const SgParams &q = unit_params<kGrouped>(p, grp, u, lu, mol);
-        const Unit w = decode_unit(q, lu);
+        const Unit w = kPair ? decode_pair(q, lu, crank) : decode_unit(q, lu);
         const CUtensorMap *ma = kGrouped ? &grp.maps[2 * mol] : &tmap_a;
         const CUtensorMap *mb = kGrouped ? &grp.maps[2 * mol + 1] : &tmap_b;
-        for (int t = 0; t < w.s && ok; ++t) {
-          for (int u0 = 0; u0 <= w.s - 1 - t && ok; u0 += 2) {
-            const bool two = u0 + 1 <= w.s - 1 - t;
-            for (int kt = 0; kt < w.ktiles; ++kt) {
-              const uint32_t stage = it % kStages;
-              const uint32_t ph = (it / kStages) & 1;
-              if (!wait_bounded(&empty[stage], ph ^ 1, abort_flag, p.status)) {
-                ok = false;
-                break;
+        const int nch = num_chunks(w.ktiles);
+        for (int c = 0; c < nch && ok; ++c) {
+          const int kb = chunk_begin(w.ktiles, nch, c), ke = chunk_begin(w.ktiles, nch, c + 1);
+          for (int t = 0; t < w.s && ok; ++t) {
+            for (int u0 = 0; u0 <= w.s - 1 - t && ok; u0 += 2) {
+              const bool two = u0 + 1 <= w.s - 1 - t;
+              for (int kt = kb; kt < ke; ++kt) {
+                const uint32_t stage = it % NS;
+                const uint32_t ph = (it / NS) & 1;
+                if (!wait_bounded<kPair>(&empty[stage], ph ^ 1, abort_flag, p.status)) {
+                  ok = false;
+                  break;
+                }
+                uint8_t *sa = smem + stage * SB;
+                uint8_t *sb = sa + kTileBytes;
+                const int kc = (w.kt0 + kt) * kKTile;
+                if (kPair) {
+                  // rank r holds B_{u0+r}; a single pair leaves rank 1's B
+                  // rows unloaded (their MMA columns 128-255 are not read).
+                  // Both CTAs' copies complete on rank 0's barrier.
+                  const bool loadb = two || crank == 0;
+                  const uint32_t fb = full0 + stage * (uint32_t)sizeof(uint64_t);
+                  if (crank == 0) mbar_expect_tx(&full[stage], two ? 4 * kTileBytes : 3 * kTileBytes);
+                  tma_load_3d_pair(sa, ma, fb, kc, w.m0, w.az0 + t * w.azs);
+                  if (loadb) tma_load_3d_pair(sb, mb, fb, kc, w.n0, w.bz0 + (u0 + crank) * w.bzs);
+                } else {
+                  mbar_expect_tx(&full[stage], two ? 3 * kTileBytes : 2 * kTileBytes);
+                  tma_load_3d(sa, ma, &full[stage], kc, w.m0, w.az0 + t * w.azs);
+                  tma_load_3d(sb, mb, &full[stage], kc, w.n0, w.bz0 + u0 * w.bzs);
+                  if (two) tma_load_3d(sb + kTileBytes, mb, &full[stage], kc, w.n0, w.bz0 + (u0 + 1) * w.bzs);
+                }
+                ++it;
               }
-              uint8_t *sa = smem + stage * kStageBytes;
-              uint8_t *sb = sa + kTileBytes;
-              const int kc = (w.kt0 + kt) * kKTile;
-              mbar_expect_tx(&full[stage], two ? 3 * kTileBytes : 2 * kTileBytes);
-              tma_load_3d(sa, ma, &full[stage], kc, w.m0, w.az0 + t * w.azs);
-              tma_load_3d(sb, mb, &full[stage], kc, w.n0, w.bz0 + u0 * w.bzs);
-              if (two) tma_load_3d(sb + kTileBytes, mb, &full[stage], kc, w.n0, w.bz0 + (u0 + 1) * w.bzs);
-              ++it;
             }
           }
         }
       }
-      if (!ok) {
+      if (!ok && crank == 0) {
         // let the copies already issued land before the CTA goes away
-        const uint32_t first = it > (uint32_t)kStages ? it - kStages : 0u;
+        const uint32_t first = it > (uint32_t)NS ? it - NS : 0u;
         for (uint32_t j = first; j < it; ++j)
-          wait_bounded(&full[j % kStages], (j / kStages) & 1, abort_flag, p.status, false);
+          wait_bounded<kPair>(&full[j % NS], (j / NS) & 1, abort_flag, p.status, false);
+      } else if (!ok) {
+        // pair, rank 1: its copies complete on rank 0's barrier, which this
+        // CTA cannot wait on; a copy lands within microseconds, so give the
+        // ones in flight a fixed 200 us
+        const uint64_t t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 < 200000ull) {
+        }
+      } else if (kPair) {
+        // the MMA commits of the last stages arrive from rank 0: let them
+        // land before this CTA can leave
+        const uint32_t first = it > (uint32_t)NS ? it - NS : 0u;
+        for (uint32_t j = first; j < it; ++j)
+          wait_bounded<kPair>(&empty[j % NS], (j / NS) & 1, abort_flag, p.status, false);
       }
     }
+  } else if (warp == 1 && kPair && crank != 0) {
+    // pair, rank 1: rank 0's thread issues the MMAs of both CTAs
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
     uint32_t it = 0, qc = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+    for (int u = first_unit; u < total_units && ok; u += unit_stride) {
       int lu, mol;
       const SgParams &q = unit_params<kGrouped>(p, grp, u, lu, mol);
-      const Unit w = decode_unit(q, lu);
-      for (int t = 0; t < w.s && ok; ++t) {
-        for (int u0 = 0; u0 <= w.s - 1 - t && ok; u0 += 2) {
-          const bool two = u0 + 1 <= w.s - 1 - t;
-          const uint32_t idesc = two ? kIdesc256 : kIdesc128;
-          int chunk_pos = 0;
-          for (int kt = 0; kt < w.ktiles; ++kt) {
-            const uint32_t stage = it % kStages;
-            const uint32_t ph = (it / kStages) & 1;
+      const Unit w = kPair ? decode_pair(q, lu, crank) : decode_unit(q, lu);
+      const int nch = num_chunks(w.ktiles);
+      for (int c = 0; c < nch && ok; ++c) {
+        const int kb = chunk_begin(w.ktiles, nch, c), ke = chunk_begin(w.ktiles, nch, c + 1);
+        for (int t = 0; t < w.s && ok; ++t) {
+          for (int u0 = 0; u0 <= w.s - 1 - t && ok; u0 += 2) {
+            const bool two = u0 + 1 <= w.s - 1 - t;
+            const uint32_t idesc = kPair ? kIdescPair : (two ? kIdesc256 : kIdesc128);
             const uint32_t buf = qc % kAccBufs;
-            if (chunk_pos == 0) {
-              if (!wait_bounded(&acc_empty[buf], ((qc / kAccBufs) & 1) ^ 1, abort_flag, p.status)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-            }
-            if (!wait_bounded(&full[stage], ph, abort_flag, p.status)) {
+            if (!wait_bounded<kPair>(&acc_empty[buf], ((qc / kAccBufs) & 1) ^ 1, abort_flag, p.status)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            if (lane == 0) {
-              const uint32_t sa = smem_u32(smem + stage * kStageBytes);
-              const uint32_t sb = sa + kTileBytes;
-              const uint32_t dt = tmem_base + buf * kAccCols;
+            for (int kt = kb; kt < ke; ++kt) {
+              const uint32_t stage = it % NS;
+              const uint32_t ph = (it / NS) & 1;
+              if (!wait_bounded<kPair>(&full[stage], ph, abort_flag, p.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              if (lane == 0) {
+                const uint32_t sa = smem_u32(smem + stage * SB);
+                const uint32_t sb = sa + kTileBytes;
+                const uint32_t dt = tmem_base + buf * kAccCols;
 #pragma unroll
-              for (int k = 0; k < kKTile / 16; ++k)
-                umma_bf16(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc,
-                          (chunk_pos > 0 || k > 0) ? 1u : 0u);
-              umma_commit(&empty[stage]);
+                for (int k = 0; k < kKTile / 16; ++k) {
+                  if (kPair)
+                    umma_bf16_pair(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc,
+                                   (kt > kb || k > 0) ? 1u : 0u);
+                  else
+                    umma_bf16(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc,
+                              (kt > kb || k > 0) ? 1u : 0u);
+                }
+                if (kPair)
+                  umma_commit_pair(&empty[stage]);
+                else
+                  umma_commit(&empty[stage]);
+              }
+              __syncwarp();
+              ++it;
+            }
+            if (!ok) break;
+            if (lane == 0) {
+              if (kPair)
+                umma_commit_pair(&acc_full[buf]);
+              else
+                umma_commit(&acc_full[buf]);
             }
             __syncwarp();
-            ++it;
-            ++chunk_pos;
-            if (chunk_pos == kChunkStages || kt == w.ktiles - 1) {
-              if (lane == 0) umma_commit(&acc_full[buf]);
-              __syncwarp();
-              ++qc;
-              chunk_pos = 0;
-            }
+            ++qc;
           }
         }
       }
@@ -413,8 +601,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!ok && lane == 0) {
       // wait for the MMAs already issued before the TMEM is released
       uint64_t *done = &acc_full[qc % kAccBufs];
-      umma_commit(done);
-      wait_bounded(done, (qc / kAccBufs) & 1, abort_flag, p.status, false);
+      if (kPair)
+        umma_commit_pair(done);
+      else
+        umma_commit(done);
+      wait_bounded<kPair>(done, (qc / kAccBufs) & 1, abort_flag, p.status, false);
     }
     __syncwarp();
   } else if (warp < kEpiWarp0) {
@@ -426,13 +617,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int half = (warp - kEpiWarp0) >> 2;
     const int row = quad * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
+    // the buffer is handed back to the MMA issuer: this CTA's, or rank 0's in a pair
+    const uint32_t acc_empty0 = kPair ? peer_addr(acc_empty, 0) : 0u;
     long long R[64];
     uint32_t qc = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+    for (int u = first_unit; u < total_units && ok; u += unit_stride) {
       int lu, mol;
       const SgParams &q = unit_params<kGrouped>(p, grp, u, lu, mol);
-      const Unit w = decode_unit(q, lu);
+      const Unit w = kPair ? decode_pair(q, lu, crank) : decode_unit(q, lu);
       const int s = w.s;
       const int T = kMode == kModeRaw ? 0 : q.shiftT[s];
       const int m = w.m0 + row;
@@ -442,47 +635,50 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int kexp_base = -14 - 8 * (s - 1) + T;
 #pragma unroll
       for (int j = 0; j < 64; ++j) R[j] = 0;
-      const int nch = (w.ktiles + kChunkStages - 1) / kChunkStages;
-      for (int t = 0; t < s && ok; ++t) {
-        for (int u0 = 0; u0 <= s - 1 - t && ok; u0 += 2) {
-          const bool two = u0 + 1 <= s - 1 - t;
-          const int g0 = t + u0;
-          const int sh0 = kMode == kModeRaw ? 0 : 8 * (s - 1 - g0) - T;
-          const int sh1 = sh0 - 8;
-          for (int c = 0; c < nch; ++c) {
+      const int nch = num_chunks(w.ktiles);
+      for (int c = 0; c < nch && ok; ++c) {
+        for (int t = 0; t < s && ok; ++t) {
+          for (int u0 = 0; u0 <= s - 1 - t && ok; u0 += 2) {
+            const bool two = u0 + 1 <= s - 1 - t;
+            const int g0 = t + u0;
+            const int sh0 = kMode == kModeRaw ? 0 : 8 * (s - 1 - g0) - T;
+            const int sh1 = sh0 - 8;
             const uint32_t buf = qc % kAccBufs;
-            if (!wait_bounded(&acc_full[buf], (qc / kAccBufs) & 1, abort_flag, p.status)) {
+            if (!wait_bounded<kPair>(&acc_full[buf], (qc / kAccBufs) & 1, abort_flag, p.status)) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t acc = lane_base + buf * kAccCols;
+            // 16 columns of each half at a time keeps 32 loaded values live
+            // next to the 64 int64 totals (no register spills)
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              uint32_t a0[16], a1[16], b0[16], b1[16];
-              tmem_ld16(acc + hh * 32, a0);
-              tmem_ld16(acc + hh * 32 + 16, a1);
-              if (two) {
-                tmem_ld16(acc + 128 + hh * 32, b0);
-                tmem_ld16(acc + 128 + hh * 32 + 16, b1);
-              }
+            for (int qq = 0; qq < 4; ++qq) {
+              uint32_t a0[16], b0[16];
+              tmem_ld16(acc + qq * 16, a0);
+              if (two) tmem_ld16(acc + 128 + qq * 16, b0);
               tmem_wait_ld();
-              if (hh == 1) {
+              if (qq == 3) {
                 // the chunk is in registers: hand the buffer back to the MMA warp
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                if (lane == 0) {
+                  if (kPair)
+                    mbar_arrive_remote(acc_empty0 + buf * (uint32_t)sizeof(uint64_t));
+                  else
+                    mbar_arrive(&acc_empty[buf]);
+                }
               }
               if (kMode == kModeRaw) {
                 if (m < q.m_valid) {
 #pragma unroll
-                  for (int j = 0; j < 32; ++j) {
-                    const int n = n_base + hh * 32 + j;
+                  for (int j = 0; j < 16; ++j) {
+                    const int n = n_base + qq * 16 + j;
                     if (n >= q.n_valid) continue;
-                    const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
+                    const int v0 = __float2int_rz(__uint_as_float(a0[j]));
                     q.raw[((long long)g0 * q.n_valid + n) * q.m_valid + m] += (long long)v0;
                     if (two) {
-                      const int v1 = __float2int_rz(__uint_as_float(j < 16 ? b0[j] : b1[j - 16]));
+                      const int v1 = __float2int_rz(__uint_as_float(b0[j]));
                       q.raw[((long long)(g0 + 1) * q.n_valid + n) * q.m_valid + m] += (long long)v1;
                     }
                   }
@@ -491,26 +687,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // both weights are non-negative powers of two, 2^8 apart:
                 // v0 2^sh0 + v1 2^sh1 = (v0 2^8 + v1) 2^sh1, exact in int64
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
-                  const int v1 = __float2int_rz(__uint_as_float(j < 16 ? b0[j] : b1[j - 16]));
+                for (int j = 0; j < 16; ++j) {
+                  const int v0 = __float2int_rz(__uint_as_float(a0[j]));
+                  const int v1 = __float2int_rz(__uint_as_float(b0[j]));
                   const long long w2 = ((long long)v0 << 8) + (long long)v1;
-                  R[hh * 32 + j] += w2 << sh1;
+                  R[qq * 16 + j] += w2 << sh1;
                 }
               } else if (!two && sh0 >= 0) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
-                  R[hh * 32 + j] += (long long)v0 << sh0;
+                for (int j = 0; j < 16; ++j) {
+                  const int v0 = __float2int_rz(__uint_as_float(a0[j]));
+                  R[qq * 16 + j] += (long long)v0 << sh0;
                 }
               } else {
                 // some low-order group falls below the kept bits (T > 0): rounded shifts
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  const int v0 = __float2int_rz(__uint_as_float(j < 16 ? a0[j] : a1[j - 16]));
+                for (int j = 0; j < 16; ++j) {
+                  const int v0 = __float2int_rz(__uint_as_float(a0[j]));
                   long long add = weigh(v0, sh0);
-                  if (two) add += weigh(__float2int_rz(__uint_as_float(j < 16 ? b0[j] : b1[j - 16])), sh1);
-                  R[hh * 32 + j] += add;
+                  if (two) add += weigh(__float2int_rz(__uint_as_float(b0[j])), sh1);
+                  R[qq * 16 + j] += add;
                 }
               }
             }
@@ -524,10 +720,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
+  // neither CTA of a pair frees its TMEM or leaves while the other may still
+  // use its barriers, shared memory or accumulators
+  if (kPair) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
-                 : "memory");
+    if (kPair)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                   : "memory");
   }
 }
 
@@ -595,17 +798,82 @@ cudaError_t launch_mode(const SgParams &p, const CUtensorMap &ta, const CUtensor
                         cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<kMode, kGrouped>,
+    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<kMode, kGrouped, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  slice_gemm_kernel<kMode, kGrouped><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, p, g);
+  slice_gemm_kernel<kMode, kGrouped, false><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, p, g);
   return cudaGetLastError();
+}
+
+// CTA-pair launch: clusters of two CTAs, as many clusters as fit at once
+// (at most one per tile pair), persistent over the tile pairs.
+template <int kMode>
+cudaError_t launch_pair(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
+  auto kern = slice_gemm_kernel<kMode, false, true>;
+  static int max_clusters = 0;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (!max_clusters) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(2 * (unsigned)(slice_gemm_grid(1 << 30) / 2), 1, 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = slice_gemm_grid(1 << 30) / 2;
+    }
+    max_clusters = n > 0 ? n : 1;
+  }
+  const int nc = p.npairs < max_clusters ? p.npairs : max_clusters;
+  cfg.gridDim = dim3(2 * (unsigned)nc, 1, 1);
+  SgGroup g;
+  std::memset(&g, 0, sizeof(g));
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, p, g);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+long long slice_gemm_pairs(const SgParams &p) {
+  if (p.layout == kLayoutKPart) {
+    const long long nt = p.nt_m, na = (nt + 1) / 2;
+    return na * (nt - na + 1) * p.nblk * p.nsplit;
+  }
+  if (p.nt_m % 2) return 0;
+  return (long long)(p.nt_m / 2) * p.nt_n;
+}
+
+// Whether a launch runs in CTA-pair mode.  p.pair: 0 never, 1 where it pays
+// (every first-GEMM tile pair is useful; the second GEMM's pairs recompute
+// one lower tile per pair of tile rows, under 1/6 extra work from 6 tile rows
+// on), 2 wherever the layout pairs.
+static bool use_pairs(const SgParams &p) {
+  if (p.pair == 0 || (p.mode != kModeX && p.mode != kModeKPart)) return false;
+  const long long np = slice_gemm_pairs(p);
+  if (np <= 0 || np > (1ll << 30)) return false;
+  if (p.pair == 2) return true;
+  return p.mode == kModeX || p.nt_m >= 6;
 }
 
 cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
   if (p.nunits <= 0) return cudaSuccess;
+  if (use_pairs(p)) {
+    SgParams q = p;
+    q.npairs = (int)slice_gemm_pairs(p);
+    if (p.mode == kModeX) return launch_pair<kModeX>(q, ta, tb, st);
+    return launch_pair<kModeKPart>(q, ta, tb, st);
+  }
   SgGroup g;
   std::memset(&g, 0, sizeof(g));
   const int grid = slice_gemm_grid(p.nunits);

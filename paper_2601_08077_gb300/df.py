@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdf.so")
 
 S_MAX = 8
 AUX_BLOCK = 128
+OPT_CLUSTER_PAIRS = 1  # DF_OPT_CLUSTER_PAIRS
 PHASES = ("split_C", "gemm1", "split_X", "gemm2", "reduce", "rho", "coulomb", "energy")
 
 _STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA or cuBLAS call failed", -3: "device allocation failed",
@@ -71,6 +72,7 @@ def lib():
         L.df_strerror.argtypes = [I]
         L.df_strerror.restype = ctypes.c_char_p
         L.df_set_profiling.argtypes = [P, I]
+        L.df_set_option.argtypes = [P, I, I]
         L.df_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         PP = ctypes.POINTER(ctypes.c_void_p)
         L.df_batch_create.argtypes = [pp, PP, I]
@@ -248,6 +250,10 @@ class Context:
 
     def set_profiling(self, on: bool):
         _check(lib().df_set_profiling(self._h, 1 if on else 0), "df_set_profiling")
+
+    def set_cluster_pairs(self, mode: int):
+        """DF_OPT_CLUSTER_PAIRS: 0 never (default), 1 where every pair is useful, 2 always."""
+        _check(lib().df_set_option(self._h, OPT_CLUSTER_PAIRS, int(mode)), "df_set_option")
 
     def phase_times(self):
         """{phase: (total ms, records)} since the last read (waits for the events)."""

@@ -285,3 +285,81 @@ def test_medium_sweep_against_fp64_oracle(df, medium):
     EJ, EJ2, EK = ctx.energy(Dg, J, K8, rho)
     EJ_ref, EK_ref = O.energies(D, J_ref, Kfp)
     assert abs(EJ - EJ_ref) <= 1e-9 and abs(EK - EK_ref) <= 1e-9
+
+
+# --------------------------------------------------------------------------
+# CTA-pair mode (DF_OPT_CLUSTER_PAIRS): two CTAs of a cluster run one
+# M = 256 tcgen05 MMA over their two output tiles (cta_group::2), each
+# staging its own A tile and half of the stacked B operand.  It must not
+# change a bit.
+
+def _random_df(seed, naux, nao, nocc):
+    """A DF-shaped tensor (symmetric in mu, nu) and orbitals with row
+    magnitudes spread over 2^-10..1, small enough for the exact oracle."""
+    rng = np.random.default_rng(seed)
+    B = spread(rng, naux * nao, nao, spread=10).reshape(naux, nao, nao)
+    B = 0.5 * (B + B.transpose(0, 2, 1))
+    C = spread(rng, nao, nocc, spread=6)
+    return B, C
+
+
+def _build_modes(df, B, C, s, modes=(0, 2)):
+    Cg = cuda(C)
+    out = {}
+    for mode in modes:
+        ctx, _ = _ctx(df, B, C.shape[1])
+        ctx.set_cluster_pairs(mode)
+        K = ctx.build_K(Cg, s)[0] if np.isscalar(s) else ctx.build_K_blocks(Cg, s)[0]
+        out[mode] = K.cpu().numpy()
+        ctx.sync_status()
+    return out
+
+
+@pytest.mark.parametrize("s", [3, 6])
+def test_cluster_pairs_vs_oracle(df, s):
+    # nocc 140: two occupied-orbital tiles (the second ragged) pair in the
+    # first GEMM; nao 160: two AO tiles, so the second GEMM's pair at j = 0
+    # also computes the lower tile; naux 24: one ragged auxiliary block
+    B, C = _random_df(11, 24, 160, 140)
+    out = _build_modes(df, B, C, s, modes=(0, 1, 2))
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[2])
+    ref = O.emulated_exchange(B, C, s)
+    if s <= 5:
+        assert np.array_equal(out[2], ref)
+    else:
+        assert np.max(np.abs(out[2] - ref)) <= 1e-14 * np.max(np.abs(ref))
+    assert np.array_equal(out[2], out[2].T)
+
+
+def test_cluster_pairs_odd_tile_count(df):
+    # nao 300: three AO tiles, so the second tile of one pair lies past the
+    # last one (it reads zeros and stores nothing)
+    B, C = _random_df(12, 16, 300, 20)
+    out = _build_modes(df, B, C, 5)
+    assert np.array_equal(out[0], out[2])
+    assert np.array_equal(out[2], O.emulated_exchange(B, C, 5))
+
+
+def test_cluster_pairs_block_slices(df):
+    # two auxiliary blocks (128 + 2 functions) with their own slice counts
+    B, C = _random_df(13, 130, 140, 6)
+    out = _build_modes(df, B, C, [5, 3])
+    assert np.array_equal(out[0], out[2])
+    assert np.array_equal(out[2], O.emulated_exchange(B, C, [5, 3]))
+
+
+@pytest.mark.parametrize("w", [inputs.Workload("df-40atom-nao200-naux600-nocc150", 40, 150, 7000),
+                               inputs.Workload("df-60atom-nao300-naux900-nocc120", 60, 120, 7100)])
+def test_cluster_pairs_physical_inputs(df, w):
+    mol, B, C, D = inputs.make_inputs(w)
+    for s in (5, 8):
+        out = _build_modes(df, B, C, s)
+        assert np.array_equal(out[0], out[2])
+
+
+def test_cluster_pairs_option_is_checked(df, small):
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    for bad in (-1, 3):
+        with pytest.raises(df.DFError):
+            ctx.set_cluster_pairs(bad)
