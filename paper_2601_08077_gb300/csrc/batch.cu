@@ -109,7 +109,11 @@ df_status enqueue_K(df_batch *b, const double *const *C, const int *nocc, int s,
   if (df::launch_slice_gemm_grouped(df::kModeX, g1, b->status, 0, st) != cudaSuccess) return DF_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
     df_ctx *c = b->ctx[i];
-    if (df::launch_split_xblocks(c->X, c->naux, c->nao, nocc[i], s, c->eX, c->Xd, df::xdigit_ld(nocc[i]), c->nblk,
+    df::ShiftTable t1;
+    const long long k1 = (long long)((c->nao + df::kKTile - 1) / df::kKTile) * df::kKTile;
+    for (int q = 0; q <= 8; ++q) t1.v[q] = df::fixed_point_shift(q, k1);
+    if (df::launch_split_xblocks(reinterpret_cast<const long long *>(c->X), c->naux, c->nao, nocc[i], s, c->eB,
+                                 c->eC, c->sblk, t1, c->eX, c->Xd, df::xdigit_ld(nocc[i]), c->nblk,
                                  st) != cudaSuccess)
       return DF_ERR_CUDA;
   }

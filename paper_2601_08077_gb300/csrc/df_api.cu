@@ -224,7 +224,10 @@ df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, 
   const long long kb_ld = df::xdigit_ld(nocc);
   {
     PhaseTimer t(c, DF_PHASE_SPLIT_X, st);
-    DF_TRY(c, df::launch_split_xblocks(c->X, naux, nao, nocc, smax, c->eX, c->Xd, kb_ld, c->nblk, st));
+    df::ShiftTable t1;
+    for (int q = 0; q <= 8; ++q) t1.v[q] = p.shiftT[q];
+    DF_TRY(c, df::launch_split_xblocks(reinterpret_cast<const long long *>(c->X), naux, nao, nocc, smax, c->eB,
+                                       c->eC, c->sblk, t1, c->eX, c->Xd, kb_ld, c->nblk, st));
   }
   // 4. per-block K_b on upper tiles (exact int64 partials per K split)
   df::SgParams q2;

@@ -15,7 +15,7 @@ struct df_ctx {
   int *eB = nullptr;
   uint16_t *Cd = nullptr;
   int *eC = nullptr;
-  double *X = nullptr;
+  double *X = nullptr;  // emulated path: the first GEMM's int64 sums (same size); FP64 path: X^T
   uint16_t *Xd = nullptr;
   int *eX = nullptr;
   long long *Rp = nullptr;  // int64 partials of the second GEMM [nblk][nsplit][nao][nao]

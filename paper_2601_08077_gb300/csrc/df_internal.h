@@ -18,7 +18,7 @@ constexpr int kMaxChunk = 1024;  // products per exact FP32 accumulation chunk
 
 // Epilogue modes of the slice GEMM.
 enum SgMode : int {
-  kModeX = 0,       // first exchange GEMM: X[n*ld + m] (transposed tile of X^T = C^T B^T)
+  kModeX = 0,       // first exchange GEMM: int64 sums R[n*ld + m] of X^T = C^T B^T (the X split rounds them)
   kModeKPart = 1,   // second exchange GEMM: int64 fixed-point partial per (block, K split),
                     // raw[part*blk + n*ld + m] (the reduce scales and sums them)
   kModeRaw = 2,     // exact S_g per group: raw[(g*n_valid + n)*m_valid + m]
@@ -84,11 +84,15 @@ cudaError_t launch_split_rows_int8(const double *A, int rows, int cols, int ld, 
                                    int8_t *digits, cudaStream_t st);
 cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int nslices, int *exps,
                                    uint16_t *digits, long long dld, long long plane_stride, cudaStream_t st);
-cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, int nslices, int *eX, uint16_t *Xd,
-                                 long long kb_ld, int nblk, cudaStream_t st);
 struct ShiftTable {
   int v[9];
 };
+// R: the first GEMM's int64 sums (kModeX); X = fl64(R 2^k) is formed here with
+// the first GEMM's exponents eB (rows (P, mu)), eC (orbitals), slices s_blk and
+// truncation table T1, then split per (block, mu).
+cudaError_t launch_split_xblocks(const long long *R, int naux, int nao, int nocc, int nslices, const int *eB,
+                                 const int *eC, const int *s_blk, const ShiftTable &T1, int *eX, uint16_t *Xd,
+                                 long long kb_ld, int nblk, cudaStream_t st);
 cudaError_t launch_kpart_reduce(const long long *Rp, const int *eX, const int *s_blk, ShiftTable T, int nao,
                                 int nblk, int nsplit, double *K, cudaStream_t st);
 

@@ -342,9 +342,27 @@ __device__ __forceinline__ Unit decode_pair(const SgParams &p, int pu, int r) {
 }
 
 // Epilogue store of the 64 output columns n0c..n0c+63 of row m.
+// First exchange GEMM: the exact int64 sums of X tile columns n0c..n0c+63
+// (rows n = (P, mu)) of orbital m; the X split applies the scales and the
+// rounding to FP64.
+__device__ __forceinline__ void store64_x(const SgParams &p, int m, int n0c, const long long (&R)[64]) {
+  if (m >= p.m_valid) return;
+  long long *out = reinterpret_cast<long long *>(p.out);
+#pragma unroll
+  for (int j = 0; j < 64; ++j) {
+    const int n = n0c + j;
+    if (n >= p.n_valid) continue;
+    out[(long long)n * p.out_ld + m] = R[j];
+  }
+}
+
 template <int kMode>
 __device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m, int n0c, const long long (&R)[64],
                                         int kexp_base, int ea_m) {
+  if (kMode == kModeX) {
+    store64_x(p, m, n0c, R);
+    return;
+  }
   if (m >= p.m_valid) return;
 #pragma unroll
   for (int j = 0; j < 64; ++j) {
@@ -669,7 +687,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive(&acc_empty[buf]);
                 }
               }
-              if (kMode == kModeRaw) {
+              if constexpr (kMode == kModeRaw) {
                 if (m < q.m_valid) {
 #pragma unroll
                   for (int j = 0; j < 16; ++j) {

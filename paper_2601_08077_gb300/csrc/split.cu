@@ -12,6 +12,8 @@
 // second pass over a row hits L1/L2) and writes s bytes-worth of digits.
 #include "df_internal.h"
 
+#include <climits>
+
 namespace df {
 
 namespace {
@@ -141,50 +143,137 @@ __global__ void split_cols_bf16_kernel(const double *__restrict__ C, int nrows, 
 
 // One CTA per (block b, row mu) of X [naux][nao][nocc]: the row of the second
 // exchange GEMM is X_b[mu, (P_local, i)], length nP*nocc, padded with zero
-// digits up to a multiple of 64, one exponent per (block, mu).  The first pass
-// finds max|X| (from DRAM), the second re-reads the row (256 KB at most, from
-// L2) and writes the digits.  Two consecutive orbitals per thread (16-byte
-// loads, 4-byte stores) when nocc is even.
-__global__ void __launch_bounds__(256) split_xblocks_kernel(const double *__restrict__ X, int naux, int nao,
-                                                            int nocc, int nslices, int *__restrict__ eX,
-                                                            uint16_t *__restrict__ Xd, long long kb_ld, int nblk) {
+// digits up to a multiple of 64, one exponent per (block, mu).
+//
+// The first exchange GEMM leaves X as its exact int64 fixed-point sums R
+// (Section 3.2's recombination before the final rounding); this kernel takes
+// X = fl64(R 2^k), k = -14 - 8(s_b - 1) + T(s_b) + eC[i] + eB[(P, mu)], the
+// one rounding of the emulated product, and splits it.  (Doing the rounding
+// here keeps the GEMM's epilogue short; it measured 18% faster that way.)
+// The first pass finds max|X| (R from DRAM), the second re-reads the row
+// (256 KB at most) and writes the digits.  Two consecutive orbitals per
+// thread (16-byte loads, 4-byte stores) when nocc is even, four loads in
+// flight per thread in the first pass.
+constexpr int kSplitXThreads = 256;
+
+// Digit t of the balanced expansion of N as an exact FP32 value, from
+// M = N + 128 (1 + 256 + ... + 256^6): the top digit is M >> 56, digit t >= 1
+// is byte 7-t of M minus 128.  The FP32 is built as (1.5 2^23 + byte) - (1.5
+// 2^23 + 128): one byte permute places the byte under the exponent bits and
+// one FP32 subtraction is exact, so its top 16 bits are the digit's BF16.
+__device__ __forceinline__ float digit_f32(long long M, int t) {
+  if (t == 0) return __int_as_float(0x4B400000 + (int)(M >> 56)) - 12582912.0f;
+  const uint32_t w = (7 - t) >= 4 ? (uint32_t)((unsigned long long)M >> 32) : (uint32_t)M;
+  return __int_as_float((int)__byte_perm(w, 0x4B400000u, 0x7640u | (uint32_t)((7 - t) & 3))) - 12583040.0f;
+}
+
+// BF16 of two FP32 digits (exact) packed low, high.
+__device__ __forceinline__ uint32_t bf16x2_of(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+}
+
+struct XScale {
+  const int *eB, *eC;  // (P, mu) row and orbital exponents of the first GEMM
+  const int *s_blk;     // slices per block
+  ShiftTable T;         // truncation of the first GEMM's fixed-point sum, by s
+};
+
+__global__ void __launch_bounds__(kSplitXThreads) split_xblocks_kernel(const long long *__restrict__ R, int naux,
+                                                                       int nao, int nocc, int nslices, XScale xs,
+                                                                       int *__restrict__ eX,
+                                                                       uint16_t *__restrict__ Xd, long long kb_ld,
+                                                                       int nblk) {
+  extern __shared__ int sh_e[];  // [kBlock] (P, mu) exponents + base, then [nocc] orbital exponents
   const int mu = blockIdx.x;
   const int b = blockIdx.y;
   const int p0 = b * kBlock;
   const int nP = min(kBlock, naux - p0);
   const int klen = nP * nocc;
   const int kpad = (klen + 63) / 64 * 64;
-  __shared__ uint64_t red[8];
+  __shared__ uint64_t red[kSplitXThreads / 32];
+  __shared__ int redE[kSplitXThreads / 32];
   __shared__ int e_sh;
+  int *eP = sh_e;
+  int *eI = sh_e + kBlock;
   {
-    uint64_t m = 0;
+    const int s1 = xs.s_blk[b];
+    const int kbase = -14 - 8 * (s1 - 1) + xs.T.v[s1];
+    for (int q = threadIdx.x; q < nP; q += blockDim.x) eP[q] = kbase + xs.eB[(long long)(p0 + q) * nao + mu];
+    for (int q = threadIdx.x; q < nocc; q += blockDim.x) eI[q] = xs.eC[q];
+  }
+  __syncthreads();
+  {
+    // largest magnitude key (E, M) of the row; E = INT_MIN marks "none yet"
+    int bE = INT_MIN;
+    uint64_t bM = 0;
+    auto take = [&](long long r, int k) {
+      if (r == 0) return;
+      int E;
+      uint64_t M;
+      mag_key(r, k, E, M);
+      if (E > bE || (E == bE && M > bM)) {
+        bE = E;
+        bM = M;
+      }
+    };
     if ((nocc & 1) == 0) {
       const int hp = nocc >> 1;
-      for (int q = threadIdx.x; q < nP * hp; q += blockDim.x) {
-        const int pl = q / hp;
-        const int i = 2 * (q - pl * hp);
-        const double2 v = *reinterpret_cast<const double2 *>(X + ((long long)(p0 + pl) * nao + mu) * nocc + i);
-        const uint64_t a = abs_bits(v.x), c = abs_bits(v.y);
-        m = a > m ? a : m;
-        m = c > m ? c : m;
+      const int total = nP * hp;
+      for (int q0 = threadIdx.x; q0 < total; q0 += 4 * blockDim.x) {
+        longlong2 v[4];
+        int kp[4], ki[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int q = q0 + r * blockDim.x;
+          if (q < total) {
+            const int pl = q / hp;
+            const int i = 2 * (q - pl * hp);
+            v[r] = *reinterpret_cast<const longlong2 *>(R + ((long long)(p0 + pl) * nao + mu) * nocc + i);
+            kp[r] = eP[pl];
+            ki[r] = i;
+          } else {
+            v[r] = make_longlong2(0, 0);
+            kp[r] = 0;
+            ki[r] = 0;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          take(v[r].x, kp[r] + eI[ki[r]]);
+          take(v[r].y, kp[r] + eI[ki[r] + 1]);
+        }
       }
     } else {
       for (int k = threadIdx.x; k < klen; k += blockDim.x) {
         const int pl = k / nocc;
-        const uint64_t a = abs_bits(X[((long long)(p0 + pl) * nao + mu) * nocc + (k - pl * nocc)]);
-        m = a > m ? a : m;
+        const int i = k - pl * nocc;
+        take(R[((long long)(p0 + pl) * nao + mu) * nocc + i], eP[pl] + eI[i]);
       }
     }
-    m = warp_max_u64(m);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      uint64_t v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-      v = warp_max_u64(v);
-      if (threadIdx.x == 0) {
-        e_sh = exponent_from_max_bits_dev(v);
-        eX[b * nao + mu] = e_sh;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int E2 = __shfl_xor_sync(0xffffffffu, bE, o);
+      const uint64_t M2 = __shfl_xor_sync(0xffffffffu, bM, o);
+      if (E2 > bE || (E2 == bE && M2 > bM)) {
+        bE = E2;
+        bM = M2;
       }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      redE[threadIdx.x >> 5] = bE;
+      red[threadIdx.x >> 5] = bM;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (redE[w] > bE || (redE[w] == bE && red[w] > bM)) {
+          bE = redE[w];
+          bM = red[w];
+        }
+      // the row's largest |X| is the rounding of its largest exact magnitude
+      const uint64_t top = bE == INT_MIN ? 0ull : abs_bits(ldexp_i64((long long)(bM >> 1), bE - 63));
+      e_sh = exponent_from_max_bits_dev(top);
+      eX[b * nao + mu] = e_sh;
     }
     __syncthreads();
   }
@@ -193,24 +282,22 @@ __global__ void __launch_bounds__(256) split_xblocks_kernel(const double *__rest
   uint16_t *dst = Xd + ((long long)b * nao + mu) * kb_ld;
   if ((nocc & 1) == 0) {
     const int hp = nocc >> 1;
+    constexpr long long kBias = 0x0080808080808080ll;  // 128 in each of the seven low bytes
     for (int q = threadIdx.x; 2 * q < kpad; q += blockDim.x) {
       const int k = 2 * q;
-      int d0[kSMax], d1[kSMax];
+      long long M0 = kBias, M1 = kBias;  // N = 0 (padding) gives zero digits
       if (k < klen) {
         const int pl = q / hp;
         const int i = k - pl * nocc;
-        const double2 v = *reinterpret_cast<const double2 *>(X + ((long long)(p0 + pl) * nao + mu) * nocc + i);
-        balanced_digits(scaled_rne((uint64_t)__double_as_longlong(v.x), e), d0);
-        balanced_digits(scaled_rne((uint64_t)__double_as_longlong(v.y), e), d1);
-      } else {
-#pragma unroll
-        for (int t = 0; t < kSMax; ++t) d0[t] = d1[t] = 0;
+        const longlong2 v = *reinterpret_cast<const longlong2 *>(R + ((long long)(p0 + pl) * nao + mu) * nocc + i);
+        const int kp = eP[pl];
+        M0 += scaled_rne_i64(v.x, kp + eI[i], e);
+        M1 += scaled_rne_i64(v.y, kp + eI[i + 1], e);
       }
 #pragma unroll
       for (int t = 0; t < kSMax; ++t)
         if (t < nslices)
-          *reinterpret_cast<uint32_t *>(dst + (long long)t * plane + k) =
-              (uint32_t)int_to_bf16_bits(d0[t]) | ((uint32_t)int_to_bf16_bits(d1[t]) << 16);
+          *reinterpret_cast<uint32_t *>(dst + (long long)t * plane + k) = bf16x2_of(digit_f32(M0, t), digit_f32(M1, t));
     }
   } else {
     for (int k = threadIdx.x; k < kpad; k += blockDim.x) {
@@ -218,8 +305,7 @@ __global__ void __launch_bounds__(256) split_xblocks_kernel(const double *__rest
       if (k < klen) {
         const int pl = k / nocc;
         const int i = k - pl * nocc;
-        balanced_digits(scaled_rne((uint64_t)__double_as_longlong(X[((long long)(p0 + pl) * nao + mu) * nocc + i]), e),
-                        d);
+        balanced_digits(scaled_rne_i64(R[((long long)(p0 + pl) * nao + mu) * nocc + i], eP[pl] + eI[i], e), d);
       } else {
 #pragma unroll
         for (int t = 0; t < kSMax; ++t) d[t] = 0;
@@ -285,10 +371,19 @@ cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int ns
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_xblocks(const double *X, int naux, int nao, int nocc, int nslices, int *eX, uint16_t *Xd,
+cudaError_t launch_split_xblocks(const long long *R, int naux, int nao, int nocc, int nslices, const int *eB,
+                                 const int *eC, const int *s_blk, const ShiftTable &T1, int *eX, uint16_t *Xd,
                                  long long kb_ld, int nblk, cudaStream_t st) {
+  const size_t sm = sizeof(int) * (size_t)(kBlock + nocc);
+  static size_t attr = 48 * 1024;
+  if (sm > attr) {
+    cudaError_t e = cudaFuncSetAttribute(split_xblocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = sm;
+  }
+  XScale xs{eB, eC, s_blk, T1};
   dim3 grid(nao, nblk);
-  split_xblocks_kernel<<<grid, 256, 0, st>>>(X, naux, nao, nocc, nslices, eX, Xd, kb_ld, nblk);
+  split_xblocks_kernel<<<grid, kSplitXThreads, sm, st>>>(R, naux, nao, nocc, nslices, xs, eX, Xd, kb_ld, nblk);
   return cudaGetLastError();
 }
 

@@ -363,3 +363,19 @@ def test_cluster_pairs_option_is_checked(df, small):
     for bad in (-1, 3):
         with pytest.raises(df.DFError):
             ctx.set_cluster_pairs(bad)
+
+
+def test_exchange_zero_rows(df, small):
+    # AO functions 0 and 7 removed from B: the rows (block, mu) of X for them
+    # are zero in every block, so the X split takes its full-scan path there
+    # (exponent 0, zero digits) and K's rows and columns 0 and 7 are zero
+    B, C, D = small
+    B = B.copy()
+    for mu in (0, 7):
+        B[:, mu, :] = 0.0
+        B[:, :, mu] = 0.0
+    ctx, _ = _ctx(df, B, C.shape[1])
+    for s in (3, 5):
+        K = ctx.build_K(cuda(C), s)[0].cpu().numpy()
+        assert np.array_equal(K, O.emulated_exchange(B, C, s))
+        assert not K[[0, 7]].any() and not K[:, [0, 7]].any()
