@@ -52,8 +52,11 @@ def parse():
     ap.add_argument("--batch-size", type=int, default=48)
     ap.add_argument("--nslices", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cluster-pairs", type=int, choices=[0, 1, 2], default=0,
-                    help="slice GEMMs on CTA pairs (cta_group::2): 0 never, 1 where every pair is useful, 2 always")
+    ap.add_argument("--aux-blocks", type=int, default=0,
+                    help="keep only the first N 128-function auxiliary blocks of the workload (a smaller case of "
+                         "the same kernels, for profiling); 0 keeps them all")
+    ap.add_argument("--cluster-pairs", type=int, choices=[0, 1, 2], default=1,
+                    help="slice GEMMs on CTA pairs (cta_group::2): 0 never, 1 the first GEMM, 2 both GEMMs")
     return ap.parse_args()
 
 
@@ -346,6 +349,11 @@ def main():
             print(json.dumps(fn(args)), flush=True)
         return
     w = workload(args.workload)
+    if args.aux_blocks > 0 and args.aux_blocks * 128 < w.naux:
+        import types
+        naux = args.aux_blocks * 128
+        w = types.SimpleNamespace(name="%s-aux%d" % (w.name, naux), n_atoms=w.n_atoms, nocc=w.nocc, seed=w.seed,
+                                  nao=w.nao, naux=naux)
 
     if args.impl == "reference":
         if rank == 0:
@@ -367,7 +375,9 @@ def main():
     dev = torch.device("cuda", local)
     mol = inputs.molecule(w.n_atoms, w.seed)
     if w.n_atoms >= 120:
-        Bg = inputs.df_tensor_device(mol, dev)   # triangular solve on the device: seconds, not minutes
+        Bg = inputs.df_tensor_device(mol, dev, nrows=w.naux)   # triangular solve on the device
+    elif w.naux < mol.naux:
+        Bg = torch.from_numpy(inputs.df_tensor_rows(mol, w.naux)).to(dev)
     else:
         Bg = torch.from_numpy(inputs.df_tensor(mol)).to(dev)
     C = inputs.orbitals(mol.nao, w.nocc, w.seed + 1)

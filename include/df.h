@@ -255,10 +255,11 @@ int64_t df_workspace_bytes(const df_ctx *ctx);
  * df_build_K_blocks (Section 3.2's slice products) run on CTA pairs: a
  * cluster of two CTAs whose M = 256 tcgen05 MMA (cta_group::2) covers two
  * output tiles that share the stacked B operand, each CTA staging its own A
- * tile and half of B.  0 never (default: on GB300 it measured no faster than
- * one CTA per tile), 1 where every pair is useful (the first GEMM whenever
- * its occupied-orbital tiles pair up, the second from six AO tiles on), 2
- * wherever the layout pairs.
+ * tile and half of B.  0 never; 1 (default) the first GEMM whenever its
+ * occupied-orbital tiles pair up (every pair is useful there); 2 both GEMMs
+ * wherever the layout pairs (the second GEMM's pairs also compute one lower
+ * tile per pair of AO tile rows, which on GB300 costs more than pairing
+ * saves).
  *
  * Returns DF_ERR_ARG for an unknown option or value; the context is unchanged. */
 #define DF_OPT_CLUSTER_PAIRS 1

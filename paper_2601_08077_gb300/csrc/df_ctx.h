@@ -33,7 +33,7 @@ struct df_ctx {
   cublasHandle_t cublas = nullptr;
   // per-phase event timing
   bool profiling = false;
-  int pair_mode = 0;  // DF_OPT_CLUSTER_PAIRS
+  int pair_mode = 1;  // DF_OPT_CLUSTER_PAIRS
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[DF_NPHASES];
   std::vector<cudaEvent_t> pool;
   // adaptive controller (Section 3.2)

@@ -872,16 +872,14 @@ long long slice_gemm_pairs(const SgParams &p) {
   return (long long)(p.nt_m / 2) * p.nt_n;
 }
 
-// Whether a launch runs in CTA-pair mode.  p.pair: 0 never, 1 where it pays
-// (every first-GEMM tile pair is useful; the second GEMM's pairs recompute
-// one lower tile per pair of tile rows, under 1/6 extra work from 6 tile rows
-// on), 2 wherever the layout pairs.
+// Whether a launch runs in CTA-pair mode.  p.pair: 0 never; 1 the first
+// exchange GEMM (every tile pair is useful there); 2 also the second, whose
+// pairs recompute one lower tile per pair of tile rows.
 static bool use_pairs(const SgParams &p) {
   if (p.pair == 0 || (p.mode != kModeX && p.mode != kModeKPart)) return false;
   const long long np = slice_gemm_pairs(p);
   if (np <= 0 || np > (1ll << 30)) return false;
-  if (p.pair == 2) return true;
-  return p.mode == kModeX || p.nt_m >= 6;
+  return p.mode == kModeX || p.pair == 2;
 }
 
 cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {

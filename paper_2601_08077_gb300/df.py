@@ -252,7 +252,7 @@ class Context:
         _check(lib().df_set_profiling(self._h, 1 if on else 0), "df_set_profiling")
 
     def set_cluster_pairs(self, mode: int):
-        """DF_OPT_CLUSTER_PAIRS: 0 never (default), 1 where every pair is useful, 2 always."""
+        """DF_OPT_CLUSTER_PAIRS: 0 never, 1 the first exchange GEMM (default), 2 both GEMMs."""
         _check(lib().df_set_option(self._h, OPT_CLUSTER_PAIRS, int(mode)), "df_set_option")
 
     def phase_times(self):

@@ -171,18 +171,35 @@ def df_tensor_rows(mol: Molecule, nrows: int) -> np.ndarray:
     return B
 
 
-def df_tensor_device(mol: Molecule, device="cuda"):
+def _preload_torch_linalg():
+    """Load torch's CUDA linear-algebra library by absolute path.  torch opens
+    it lazily by bare name, which fails in processes whose library search path
+    has been changed (a profiler's injection, for one)."""
+    import ctypes
+    import torch
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+
+
+def df_tensor_device(mol: Molecule, device="cuda", nrows: int | None = None):
     """B of Eq. cderi with the triangular solve on a CUDA device (torch / cuBLAS).
 
     Input synthesis for the large workloads (batches, predictor training, the
     240-atom molecule): the integrals and the metric's Cholesky factor are
     formed on the host as in ``df_tensor``, the solve L B = (P|mu nu) runs on
     the device.  The result agrees with ``df_tensor`` to the conditioning of
-    the metric, not bit for bit, so parity tests use ``df_tensor``.
-    Returns a contiguous float64 tensor [naux, nao, nao] on ``device``.
+    the metric, not bit for bit, so parity tests use ``df_tensor``.  With
+    ``nrows`` only the first nrows auxiliary rows are formed (as in
+    ``df_tensor_rows``: the forward substitution needs no later rows).
+    Returns a contiguous float64 tensor [naux or nrows, nao, nao] on ``device``.
     """
     import scipy.linalg as sl
     import torch
+    _preload_torch_linalg()
+    if nrows is not None and nrows < mol.naux:
+        mol = Molecule(mol.n_atoms, mol.seed, mol.edge, mol.xyz, mol.ao_xyz, mol.ao_exp,
+                       np.ascontiguousarray(mol.aux_xyz[:nrows]), np.ascontiguousarray(mol.aux_exp[:nrows]))
     V = metric(mol)
     L = torch.from_numpy(sl.cholesky(V, lower=True, check_finite=False)).to(device)
     T = torch.from_numpy(int3c(mol).reshape(mol.naux, -1)).to(device)

@@ -379,3 +379,15 @@ def test_exchange_zero_rows(df, small):
         K = ctx.build_K(cuda(C), s)[0].cpu().numpy()
         assert np.array_equal(K, O.emulated_exchange(B, C, s))
         assert not K[[0, 7]].any() and not K[:, [0, 7]].any()
+
+
+@pytest.mark.parametrize("nocc", [19, 20])
+def test_exchange_odd_and_even_nocc(df, small, nocc):
+    # the X split's scalar path (odd nocc) and its two-orbital path (even nocc)
+    B, C, D = small
+    C = np.ascontiguousarray(C[:, :nocc])
+    ctx, _ = _ctx(df, B, nocc)
+    for s in (4, 5):
+        K = ctx.build_K(cuda(C), s)[0].cpu().numpy()
+        assert np.array_equal(K, O.emulated_exchange(B, C, s))
+    ctx.sync_status()
