@@ -55,7 +55,8 @@ constexpr int kStages = 4;
 constexpr int kTileBytes = kTile * kKTile * 2;        // one 128 x 64 BF16 box, 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;           // A_t tile + two stacked B tiles
 // CTA-pair mode (cta_group::2): a CTA stages its own A_t tile and one of the
-// two stacked B tiles, so a stage is 32 KB and six fit in the same space.
+// two stacked B tiles, so a stage is 32 KB and six fit in the space of the
+// four 48 KB stages (seven measured no faster on GB300).
 constexpr int kStagesP = 6;
 constexpr int kStageBytesP = 2 * kTileBytes;
 constexpr int kThreads = 384;                         // 12 warps
@@ -67,6 +68,8 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kChunkStages = kMaxChunk / kKTile;      // 16 stages = 1024 products
 constexpr uint64_t kTimeoutNs = 4000000000ull;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*alignment slack*/;
+constexpr int kSmemBytesP = kStagesP * kStageBytesP + 1024 /*barriers*/ + 1024 /*alignment slack*/;
+static_assert(kSmemBytesP <= 232448, "pair ring must fit the 227 KB opt-in shared memory of a CTA");
 // Register split (setmaxnreg): warps 0-3 drop to 56, the 8 epilogue warps rise
 // to 224; 128*56 + 256*224 = 64512 = 384 threads * 168 registers at launch.
 constexpr int kRegsLow = 56;
@@ -84,7 +87,6 @@ constexpr uint32_t kIdesc256 = idesc_for(256);
 // 0-127 from the first CTA's shared memory, 128-255 from the second's).
 constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
                                 ((uint32_t)(256 >> 4) << 24);
-static_assert(kStagesP * kStageBytesP <= kStages * kStageBytes, "pair ring must fit the same shared memory");
 
 struct Unit {
   int m0, n0, az0, azs, bz0, bzs, kt0, ktiles, s, blk, part;
@@ -228,8 +230,11 @@ __device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t rank) {
   return r;
 }
 
+// Arrive on a barrier of either CTA of the pair.  Default semantics: what the
+// arrival publishes (TMEM reads done) is ordered by the tcgen05 fences around
+// it, so no cluster-scope release (a full memory barrier) is needed.
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -839,12 +844,12 @@ cudaError_t launch_pair(const SgParams &p, const CUtensorMap &ta, const CUtensor
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.dynamicSmemBytes = kSmemBytesP;
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   if (!max_clusters) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytesP);
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3(2 * (unsigned)(slice_gemm_grid(1 << 30) / 2), 1, 1);
     int n = 0;
