@@ -11,11 +11,13 @@ against the native-FP64 build of the same K on the same GPU.
 
 metric: effective FP64 TFLOP/s of the exchange build, F_K = 4 nao^2 naux nocc
 (the paper's FLOP model with dense B, Section 3.1) per step, divided by the
-step time.  The inputs (B is 5.2 GB for the 120-atom molecule) are far larger
-than L2, so no flush is needed between steps.
+step time.  The default workload is the 240-atom molecule (nao 1200, naux
+3600, nocc 250; B is 41.5 GB), far larger than L2, so no flush is needed
+between steps.
 
 Usage: python bench.py [--gpus N --steps K --warmup W --impl ours|reference
-                        --workload medium|small|large --nslices S]
+                        --workload large|medium|profile|small|batch|sequence|predictor
+                        --nslices S --aux-blocks N --cluster-pairs 0|1|2]
 """
 from __future__ import annotations
 
@@ -506,7 +508,8 @@ def main():
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": recorded_traffic(kname, w.name, s, args.cluster_pairs),
                      "peak_source": "bf16_tflops_sustained (%s)" % src,
                      "algorithmic": "s(s+1)/2 slice-pair products x 2 flops per multiply-add, no padding"},
         "accuracy": {"max_dK_rel_vs_fp64": dK, "dE_vs_fp64": dE, "gate_1e-10": dK <= 1e-10},
@@ -523,6 +526,40 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# Source files whose change invalidates a recorded DRAM-traffic figure of the
+# slice GEMM (the kernel, its launch parameters and the device helpers).
+TRAFFIC_SOURCES = ("paper_2601_08077_gb300/csrc/slicegemm.cu", "paper_2601_08077_gb300/csrc/df_internal.h",
+                   "paper_2601_08077_gb300/csrc/df_device.cuh", "paper_2601_08077_gb300/csrc/df_api.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, workload_name, nslices, cluster_pairs):
+    """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + write.sum from
+    one ncu capture of this bench command), if the capture in
+    profiles/dram_traffic.txt (JSON records) matches the workload, the slice
+    count, the pair mode and the current kernel sources; else None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            recs = json.load(f)
+    except (OSError, ValueError):
+        return None
+    sha = kernel_source_sha()
+    for r in recs:
+        if (r.get("kernel") == kernel and r.get("workload") == workload_name and r.get("nslices") == nslices
+                and r.get("cluster_pairs") == cluster_pairs and r.get("source_sha256") == sha):
+            return float(r["dram_bytes_per_launch"])
+    return None
 
 
 def phases_k_ms(phases, steps):
