@@ -376,20 +376,23 @@ def main():
 
     dev = torch.device("cuda", local)
     mol = inputs.molecule(w.n_atoms, w.seed)
+    ctx = df.Context(w.nao, w.naux, w.nocc)
     if w.n_atoms >= 120:
-        Bg = inputs.df_tensor_device(mol, dev, nrows=w.naux)   # triangular solve on the device
-    elif w.naux < mol.naux:
-        Bg = torch.from_numpy(inputs.df_tensor_rows(mol, w.naux)).to(dev)
+        # the library forms B from the integrals on the device (Cholesky + triangular solve)
+        sub = inputs.leading_aux(mol, w.naux)
+        Tg = torch.from_numpy(inputs.int3c(sub)).to(dev)
+        Vg = torch.from_numpy(inputs.metric(sub)).to(dev)
+        Bg = ctx.setup_integrals(Tg, Vg)
+        del Vg
     else:
-        Bg = torch.from_numpy(inputs.df_tensor(mol)).to(dev)
+        Bh = inputs.df_tensor_rows(mol, w.naux) if w.naux < mol.naux else inputs.df_tensor(mol)
+        Bg = torch.from_numpy(Bh).to(dev)
+        ctx.setup(Bg)
     C = inputs.orbitals(mol.nao, w.nocc, w.seed + 1)
     D = inputs.density(C)
     Cg = torch.from_numpy(C).to(dev)
     Dg = torch.from_numpy(D).to(dev)
     B_bytes = Bg.numel() * 8
-    B = Bg
-    ctx = df.Context(w.nao, w.naux, w.nocc)
-    ctx.setup(Bg)
     ctx.set_cluster_pairs(args.cluster_pairs)
     J = torch.empty((w.nao, w.nao), dtype=torch.float64, device=dev)
     K = torch.empty_like(J)

@@ -83,6 +83,20 @@ df_status df_setup(df_ctx *ctx, const double *B_dev, void *stream);
  * NULL = the natural order.  DF_ERR_ARG if perm_host is not a permutation. */
 df_status df_setup_ordered(df_ctx *ctx, const double *B_dev, const int *perm_host, void *stream);
 
+/* As df_setup_ordered, forming B on the device from the integrals
+ * (Eq. cderi): B = L^{-1} (P|mu nu) with L L^T = (P|Q) the metric's Cholesky
+ * factor.  T_dev [naux][nao][nao] holds (P|mu nu) on entry and B on return
+ * (in place; caller-owned and kept alive for the context's lifetime, as in
+ * df_setup); V_dev [naux][naux] is the metric (symmetric; read only).  The
+ * factorisation (cuSOLVER potrf) and the triangular solve (cuBLAS trsm) are
+ * FP64 library steps; every B_P is then made exactly symmetric,
+ * (B_P + B_P^T)/2, and split as in df_setup.  perm_host as in
+ * df_setup_ordered (NULL = natural order).  Synchronises the stream once (to
+ * read the factorisation's status).  Returns DF_ERR_NOT_PD if the metric is
+ * not positive definite (T_dev is then unchanged), DF_ERR_OOM if the
+ * naux^2 factor workspace cannot be allocated. */
+df_status df_setup_integrals(df_ctx *ctx, double *T_dev, const double *V_dev, const int *perm_host, void *stream);
+
 /* Coulomb build in FP64 (Eqs. df-j-1, df-j-2; the paper keeps J in FP64,
  * Section 3.1).  D_dev symmetric [nao][nao]; J_dev [nao][nao] out;
  * rho_dev [naux] out (may be NULL: then an internal buffer is used). */

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdf.so")
-CU_SOURCES = ["split.cu", "slicegemm.cu", "coulomb.cu", "df_api.cu", "noalloc.cu", "batch.cu", "mlp.cu"]
+CU_SOURCES = ["split.cu", "slicegemm.cu", "coulomb.cu", "df_api.cu", "noalloc.cu", "batch.cu", "mlp.cu", "cderi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -63,7 +63,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, verbose), CU_SOURCES))
     tmp = LIB + ".tmp%d" % os.getpid()
     lib64 = os.path.join(_cuda_home(), "lib64")
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L" + lib64, "-Xlinker", "-rpath=" + lib64, "-lcublas"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L" + lib64, "-Xlinker", "-rpath=" + lib64, "-lcublas", "-lcusolver"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -18,6 +18,8 @@
 
 #include "df_ctx.h"
 
+#include <cusolverDn.h>
+
 namespace {
 
 using df::kBlock;
@@ -363,6 +365,7 @@ void df_destroy(df_ctx *c) {
     }
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->cublas) cublasDestroy(c->cublas);
+  if (c->cusolver) cusolverDnDestroy(reinterpret_cast<cusolverDnHandle_t>(c->cusolver));
   delete c;
 }
 

@@ -31,6 +31,7 @@ struct df_ctx {
   int64_t bytes = 0;
   df_status last = DF_OK;
   cublasHandle_t cublas = nullptr;
+  void *cusolver = nullptr;  // cusolverDnHandle_t, created by df_setup_integrals
   // per-phase event timing
   bool profiling = false;
   int pair_mode = 1;  // DF_OPT_CLUSTER_PAIRS

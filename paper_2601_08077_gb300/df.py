@@ -53,6 +53,7 @@ def lib():
         L.df_destroy.restype = None
         L.df_setup.argtypes = [P, P, V]
         L.df_setup_ordered.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), V]
+        L.df_setup_integrals.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_int), V]
         L.df_build_J.argtypes = [P, P, P, P, V]
         L.df_build_K.argtypes = [P, P, I, I, P, ctypes.POINTER(KStats), V]
         L.df_build_K_blocks.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(KStats), V]
@@ -202,6 +203,15 @@ class Context:
         else:
             arr = (ctypes.c_int * self.naux)(*[int(x) for x in perm])
             _check(lib().df_setup_ordered(self._h, _f64(B), arr, _stream(stream)), "df_setup_ordered")
+
+    def setup_integrals(self, T: torch.Tensor, V: torch.Tensor, perm=None, stream=None):
+        """Form B = L^{-1} T in place on the device (L L^T = V) and attach it; returns T (now B)."""
+        assert T.shape == (self.naux, self.nao, self.nao) and V.shape == (self.naux, self.naux)
+        assert T.dtype == torch.float64 and V.dtype == torch.float64 and T.is_contiguous() and V.is_contiguous()
+        self._B = T
+        arr = None if perm is None else (ctypes.c_int * self.naux)(*[int(x) for x in perm])
+        _check(lib().df_setup_integrals(self._h, _f64(T), _f64(V), arr, _stream(stream)), "df_setup_integrals")
+        return T
 
     def build_J(self, D, J=None, rho=None, stream=None):
         if J is None:

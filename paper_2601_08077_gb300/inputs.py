@@ -149,6 +149,14 @@ def df_tensor(mol: Molecule) -> np.ndarray:
     return B
 
 
+def leading_aux(mol: Molecule, nrows: int) -> Molecule:
+    """The same molecule with only its first nrows auxiliary functions."""
+    if nrows >= mol.naux:
+        return mol
+    return Molecule(mol.n_atoms, mol.seed, mol.edge, mol.xyz, mol.ao_xyz, mol.ao_exp,
+                    np.ascontiguousarray(mol.aux_xyz[:nrows]), np.ascontiguousarray(mol.aux_exp[:nrows]))
+
+
 def df_tensor_rows(mol: Molecule, nrows: int) -> np.ndarray:
     """The first nrows auxiliary rows of B (Eq. cderi), without forming the rest.
 

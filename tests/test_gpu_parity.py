@@ -391,3 +391,34 @@ def test_exchange_odd_and_even_nocc(df, small, nocc):
         K = ctx.build_K(cuda(C), s)[0].cpu().numpy()
         assert np.array_equal(K, O.emulated_exchange(B, C, s))
     ctx.sync_status()
+
+
+def test_setup_from_integrals(df, small):
+    # B = L^{-1} (P|mu nu) on the device against the oracle's own Cholesky and
+    # forward substitution, within the forward-error bound n u sqrt(cond V) |B|
+    mol = inputs.molecule(inputs.SMALL.n_atoms, inputs.SMALL.seed)
+    T = inputs.int3c(mol)
+    V = inputs.metric(mol)
+    Bo = O.df_tensor(T, V)
+    ctx = df.Context(mol.nao, mol.naux, 20)
+    Bg = ctx.setup_integrals(cuda(T), cuda(V)).cpu().numpy()
+    tol = V.shape[0] * 2.0 ** -52 * math.sqrt(np.linalg.cond(V)) * np.max(np.abs(Bo))
+    assert np.max(np.abs(Bg - Bo)) <= tol
+    assert np.array_equal(Bg, Bg.transpose(0, 2, 1))
+    # the attached B drives the builds: K is the oracle's emulation of that B
+    B, C, D = small
+    K = ctx.build_K(cuda(C), 5)[0].cpu().numpy()
+    assert np.array_equal(K, O.emulated_exchange(Bg, C, 5))
+
+
+def test_setup_from_integrals_rejects_indefinite_metric(df):
+    naux, nao = 8, 4
+    T = np.random.default_rng(3).standard_normal((naux, nao, nao))
+    V = np.eye(naux)
+    V[5, 5] = -1.0
+    ctx = df.Context(nao, naux, 2)
+    Tg = cuda(T)
+    with pytest.raises(df.DFError) as e:
+        ctx.setup_integrals(Tg, cuda(V))
+    assert e.value.status == -4  # DF_ERR_NOT_PD
+    assert np.array_equal(Tg.cpu().numpy(), T)
