@@ -77,7 +77,7 @@ df_status build_tables(df_batch *b, const int *nocc) {
     df_ctx *c = b->ctx[i];
     const int ns = std::max(1, std::min(b->nsplit_cap, c->nsplit));
     b->nsplit[i] = ns;
-    if (!df::gemm1_setup(c, nocc[i], p1[k], m1[2 * k], m1[2 * k + 1])) return DF_ERR_CUDA;
+    if (!df::gemm1_setup(c, nocc[i], p1[k], m1[2 * k], m1[2 * k + 1], false)) return DF_ERR_CUDA;
     if (!df::gemm2_setup(c, nocc[i], ns, p2[k], m2[2 * k])) return DF_ERR_CUDA;
     m2[2 * k + 1] = m2[2 * k];
     o1[k + 1] = o1[k] + p1[k].nunits;

@@ -132,10 +132,44 @@ namespace df {
 
 df_status ctx_upload_slices(df_ctx *c, const int *sb, cudaStream_t st) { return upload_slices(c, sb, st); }
 
-// Parameters and operand maps of the first exchange GEMM (X^T = C^T B^T).
-bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb) {
+// Parameters and operand maps of the first exchange GEMM: X^T = C^T B^T (the
+// orbitals on the MMA's M side), or, when CTA pairs are on and the orbitals
+// fit one 128-row tile, X = B C with the (P, mu) rows on the M side (pairs of
+// those tiles share the stacked C slices; nao even keeps a pair inside one
+// auxiliary block, so both CTAs run the same slice count).  X lands as
+// [(P, mu)][i] either way.
+bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb, bool allow_swap) {
   const int nao = c->nao, naux = c->naux;
   const long long c_plane = (long long)c->nocc_max * c->ld_nao;
+  const bool swapped = allow_swap && c->pair_mode >= 1 && nocc <= kTile && (nao & 1) == 0;
+  if (swapped) {
+    if (!make_tmap_bf16(&ta, c->Bd, nao, (long long)naux * nao, c->s_max, c->ld_nao,
+                        (long long)naux * nao * c->ld_nao))
+      return false;
+    if (!make_tmap_bf16(&tb, c->Cd, nao, nocc, c->s_max, c->ld_nao, c_plane)) return false;
+    std::memset(&p, 0, sizeof(p));
+    p.layout = kLayoutXs;
+    p.mode = kModeXs;
+    p.nt_m = (int)(((long long)naux * nao + kTile - 1) / kTile);
+    p.nt_n = (nocc + kTile - 1) / kTile;
+    p.nunits = p.nt_m * p.nt_n;
+    p.m_valid = naux * nao;
+    p.n_valid = nocc;
+    p.ktiles = (nao + kKTile - 1) / kKTile;
+    p.nao = nao;
+    p.nocc = nocc;
+    p.nblk = c->nblk;
+    p.naux = naux;
+    p.s_blk = c->sblk;
+    for (int q = 0; q <= 8; ++q) p.shiftT[q] = fixed_point_shift(q, (long long)p.ktiles * kKTile);
+    p.ea = c->eB;
+    p.eb = c->eC;
+    p.out = c->X;
+    p.out_ld = nocc;
+    p.status = c->status;
+    p.pair = c->pair_mode;
+    return true;
+  }
   if (!make_tmap_bf16(&ta, c->Cd, nao, nocc, c->s_max, c->ld_nao, c_plane)) return false;
   if (!make_tmap_bf16(&tb, c->Bd, nao, (long long)naux * nao, c->s_max, c->ld_nao, (long long)naux * nao * c->ld_nao))
     return false;

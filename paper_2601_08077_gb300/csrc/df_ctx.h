@@ -48,7 +48,9 @@ namespace df {
 // the stream when they did; not allowed during stream capture).
 df_status ctx_upload_slices(df_ctx *c, const int *sb, cudaStream_t st);
 // Parameters and operand maps of the two exchange GEMMs of a context.
-bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb);
+// allow_swap: the (P, mu)-rows-on-M layout may be chosen (single-problem
+// launches; the grouped launch runs every problem in the orbitals-on-M one).
+bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb, bool allow_swap = true);
 bool gemm2_setup(df_ctx *c, int nocc, int nsplit, SgParams &q2, CUtensorMap &tx);
 long long xdigit_ld(int nocc);
 }  // namespace df

@@ -23,6 +23,8 @@ enum SgMode : int {
                     // raw[part*blk + n*ld + m] (the reduce scales and sums them)
   kModeRaw = 2,     // exact S_g per group: raw[(g*n_valid + n)*m_valid + m]
   kModeGemm = 3,    // generic emulated product: out[m*ld + n]
+  kModeXs = 4,      // first exchange GEMM with swapped operands (rows (P, mu) on the A side):
+                    // int64 sums R[m*ld + n], the same X layout as kModeX
 };
 
 // How the persistent kernel turns a unit index into a tile.
@@ -30,6 +32,7 @@ enum SgLayout : int {
   kLayoutGrid = 0,   // u -> (m_tile = u % nt_m, n_tile = u / nt_m), planes az = t, bz = t
   kLayoutX = 1,      // first exchange GEMM: n rows are (P, mu); block = n0 / (128 nao)
   kLayoutKPart = 2,  // second exchange GEMM: u -> (upper tile pair, block)
+  kLayoutXs = 3,     // first exchange GEMM, swapped: m rows are (P, mu); block = m0 / (128 nao)
 };
 
 struct SgParams {

@@ -288,6 +288,31 @@ __device__ __forceinline__ Unit kpart_unit(const SgParams &p, int i, int j, int 
   return w;
 }
 
+// Tile (mt, nt) of the grid layouts (kLayoutGrid, kLayoutX, kLayoutXs).
+__device__ __forceinline__ Unit grid_unit(const SgParams &p, int mt, int nt) {
+  Unit w;
+  w.m0 = mt * kTile;
+  w.n0 = nt * kTile;
+  w.az0 = 0;
+  w.azs = 1;
+  w.bz0 = 0;
+  w.bzs = 1;
+  w.kt0 = 0;
+  w.part = 0;
+  w.ktiles = p.ktiles;
+  if (p.layout == kLayoutX || p.layout == kLayoutXs) {
+    // the (P, mu) rows of a 128-function block: a tile never straddles two blocks
+    const long long r0 = p.layout == kLayoutX ? (long long)w.n0 : (long long)w.m0;
+    w.blk = (int)(r0 / ((long long)kBlock * p.nao));
+    if (w.blk >= p.nblk) w.blk = p.nblk - 1;  // a tile past the last row (pairs): any valid count
+    w.s = p.s_blk[w.blk];
+  } else {
+    w.blk = 0;
+    w.s = p.s_fixed;
+  }
+  return w;
+}
+
 __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
   Unit w;
   if (p.layout == kLayoutKPart) {
@@ -300,27 +325,8 @@ __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
       ++i;
     }
     return kpart_unit(p, i, i + rem, u / npairs);
-  } else {
-    const int mt = u % p.nt_m;
-    const int nt = u / p.nt_m;
-    w.m0 = mt * kTile;
-    w.n0 = nt * kTile;
-    w.az0 = 0;
-    w.azs = 1;
-    w.bz0 = 0;
-    w.bzs = 1;
-    w.kt0 = 0;
-    w.part = 0;
-    w.ktiles = p.ktiles;
-    if (p.layout == kLayoutX) {
-      w.blk = (int)((long long)w.n0 / ((long long)kBlock * p.nao));
-      w.s = p.s_blk[w.blk];
-    } else {
-      w.blk = 0;
-      w.s = p.s_fixed;
-    }
   }
-  return w;
+  return grid_unit(p, u % p.nt_m, u / p.nt_m);
 }
 
 // Tile of CTA `r` (0 or 1) of tile pair `pu` in CTA-pair mode: both tiles
@@ -342,8 +348,8 @@ __device__ __forceinline__ Unit decode_pair(const SgParams &p, int pu, int r) {
     }
     return kpart_unit(p, 2 * a + r, 2 * a + rem, pu / per);
   }
-  const int h = p.nt_m >> 1;
-  return decode_unit(p, 2 * (pu % h) + r + p.nt_m * (pu / h));
+  const int h = (p.nt_m + 1) >> 1;  // m tiles 2a, 2a+1 (the second may lie past the last: zeros, no stores)
+  return grid_unit(p, 2 * (pu % h) + r, pu / h);
 }
 
 // Epilogue store of the 64 output columns n0c..n0c+63 of row m.
@@ -366,6 +372,15 @@ __device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m,
                                         int kexp_base, int ea_m) {
   if (kMode == kModeX) {
     store64_x(p, m, n0c, R);
+    return;
+  }
+  if (kMode == kModeXs) {
+    // swapped first GEMM: row m = (P, mu), columns n = orbitals, the same X[(P, mu)][i]
+    if (m >= p.m_valid) return;
+    long long *out = reinterpret_cast<long long *>(p.out) + (long long)m * p.out_ld;
+#pragma unroll
+    for (int j = 0; j < 64; ++j)
+      if (n0c + j < p.n_valid) out[n0c + j] = R[j];
     return;
   }
   if (m >= p.m_valid) return;
@@ -873,6 +888,7 @@ long long slice_gemm_pairs(const SgParams &p) {
     const long long nt = p.nt_m, na = (nt + 1) / 2;
     return na * (nt - na + 1) * p.nblk * p.nsplit;
   }
+  if (p.layout == kLayoutXs) return (long long)((p.nt_m + 1) / 2) * p.nt_n;  // many m tiles: one may idle
   if (p.nt_m % 2) return 0;
   return (long long)(p.nt_m / 2) * p.nt_n;
 }
@@ -881,10 +897,10 @@ long long slice_gemm_pairs(const SgParams &p) {
 // exchange GEMM (every tile pair is useful there); 2 also the second, whose
 // pairs recompute one lower tile per pair of tile rows.
 static bool use_pairs(const SgParams &p) {
-  if (p.pair == 0 || (p.mode != kModeX && p.mode != kModeKPart)) return false;
+  if (p.pair == 0 || (p.mode != kModeX && p.mode != kModeXs && p.mode != kModeKPart)) return false;
   const long long np = slice_gemm_pairs(p);
   if (np <= 0 || np > (1ll << 30)) return false;
-  return p.mode == kModeX || p.pair == 2;
+  return p.mode == kModeX || p.mode == kModeXs || p.pair == 2;
 }
 
 cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
@@ -893,6 +909,7 @@ cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CU
     SgParams q = p;
     q.npairs = (int)slice_gemm_pairs(p);
     if (p.mode == kModeX) return launch_pair<kModeX>(q, ta, tb, st);
+    if (p.mode == kModeXs) return launch_pair<kModeXs>(q, ta, tb, st);
     return launch_pair<kModeKPart>(q, ta, tb, st);
   }
   SgGroup g;
@@ -903,6 +920,7 @@ cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CU
     case kModeKPart: return launch_mode<kModeKPart, false>(p, ta, tb, g, grid, st);
     case kModeRaw: return launch_mode<kModeRaw, false>(p, ta, tb, g, grid, st);
     case kModeGemm: return launch_mode<kModeGemm, false>(p, ta, tb, g, grid, st);
+    case kModeXs: return launch_mode<kModeXs, false>(p, ta, tb, g, grid, st);
   }
   return cudaErrorInvalidValue;
 }
