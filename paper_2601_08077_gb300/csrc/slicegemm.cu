@@ -348,7 +348,13 @@ __device__ __forceinline__ Unit decode_pair(const SgParams &p, int pu, int r) {
     }
     return kpart_unit(p, 2 * a + r, 2 * a + rem, pu / per);
   }
-  const int h = (p.nt_m + 1) >> 1;  // m tiles 2a, 2a+1 (the second may lie past the last: zeros, no stores)
+  if (p.layout == kLayoutXs) {
+    // (P, mu) tiles 2a, 2a+1 (the second may lie past the last: zeros, no
+    // stores); the orbital tiles of one pair of (P, mu) tiles run back to
+    // back, so its B-digit tiles are reused from L2
+    return grid_unit(p, 2 * (pu / p.nt_n) + r, pu % p.nt_n);
+  }
+  const int h = p.nt_m >> 1;
   return grid_unit(p, 2 * (pu % h) + r, pu / h);
 }
 
