@@ -155,6 +155,7 @@ __global__ void split_cols_bf16_kernel(const double *__restrict__ C, int nrows, 
 // thread (16-byte loads, 4-byte stores) when nocc is even, four loads in
 // flight per thread in the first pass.
 constexpr int kSplitXThreads = 256;
+constexpr int kP1 = 4;  // loads in flight per thread in the first pass (8 measured slower)
 
 // Digit t of the balanced expansion of N as an exact FP32 value, from
 // M = N + 128 (1 + 256 + ... + 256^6): the top digit is M >> 56, digit t >= 1
@@ -219,11 +220,11 @@ __global__ void __launch_bounds__(kSplitXThreads) split_xblocks_kernel(const lon
     if ((nocc & 1) == 0) {
       const int hp = nocc >> 1;
       const int total = nP * hp;
-      for (int q0 = threadIdx.x; q0 < total; q0 += 4 * blockDim.x) {
-        longlong2 v[4];
-        int kp[4], ki[4];
+      for (int q0 = threadIdx.x; q0 < total; q0 += kP1 * blockDim.x) {
+        longlong2 v[kP1];
+        int kp[kP1], ki[kP1];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < kP1; ++r) {
           const int q = q0 + r * blockDim.x;
           if (q < total) {
             const int pl = q / hp;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kSplitXThreads) split_xblocks_kernel(const lon
           }
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < kP1; ++r) {
           take(v[r].x, kp[r] + eI[ki[r]]);
           take(v[r].y, kp[r] + eI[ki[r] + 1]);
         }
