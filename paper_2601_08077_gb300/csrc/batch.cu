@@ -35,6 +35,7 @@ struct df_batch {
   std::vector<int> nsplit;  // per molecule, in molecule order
   std::vector<int> nocc;
   int tables_for_s = -1;
+  bool pairs1 = false;  // first GEMM on CTA pairs (swapped layout, tables in tile pairs)
   // graph cache
   cudaGraphExec_t exec_K = nullptr, exec_J = nullptr;
   std::vector<const void *> key_K, key_J;
@@ -72,15 +73,20 @@ df_status build_tables(df_batch *b, const int *nocc) {
   std::vector<int> o1(n + 1, 0), o2(n + 1, 0);
   const std::vector<int> ord = unit_order(b, nocc);
   b->nsplit.assign(n, 1);
+  // the first GEMM runs on CTA pairs when every molecule's orbitals fit one tile
+  // (the swapped layout; one slice count per molecule, so pairs may cross blocks)
+  b->pairs1 = true;
+  for (int i = 0; i < n; ++i) b->pairs1 = b->pairs1 && b->ctx[i]->pair_mode >= 1 && nocc[i] <= df::kTile;
   for (int k = 0; k < n; ++k) {
     const int i = ord[k];
     df_ctx *c = b->ctx[i];
     const int ns = std::max(1, std::min(b->nsplit_cap, c->nsplit));
     b->nsplit[i] = ns;
-    if (!df::gemm1_setup(c, nocc[i], p1[k], m1[2 * k], m1[2 * k + 1], false)) return DF_ERR_CUDA;
+    if (!df::gemm1_setup(c, nocc[i], p1[k], m1[2 * k], m1[2 * k + 1], b->pairs1 ? 2 : 0)) return DF_ERR_CUDA;
     if (!df::gemm2_setup(c, nocc[i], ns, p2[k], m2[2 * k])) return DF_ERR_CUDA;
     m2[2 * k + 1] = m2[2 * k];
-    o1[k + 1] = o1[k] + p1[k].nunits;
+    if (b->pairs1) p1[k].npairs = (int)df::slice_gemm_pairs(p1[k]);
+    o1[k + 1] = o1[k] + (b->pairs1 ? p1[k].npairs : p1[k].nunits);
     o2[k + 1] = o2[k] + p2[k].nunits;
   }
   b->total1 = o1[n];
@@ -106,7 +112,9 @@ df_status enqueue_K(df_batch *b, const double *const *C, const int *nocc, int s,
       return DF_ERR_CUDA;
   }
   df::SgGroup g1{b->params1, b->maps1, b->off1, n, b->total1};
-  if (df::launch_slice_gemm_grouped(df::kModeX, g1, b->status, 0, st) != cudaSuccess) return DF_ERR_CUDA;
+  if (df::launch_slice_gemm_grouped(b->pairs1 ? df::kModeXs : df::kModeX, g1, b->status, 0, st, b->pairs1) !=
+      cudaSuccess)
+    return DF_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
     df_ctx *c = b->ctx[i];
     df::ShiftTable t1;

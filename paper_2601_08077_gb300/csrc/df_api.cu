@@ -138,10 +138,11 @@ df_status ctx_upload_slices(df_ctx *c, const int *sb, cudaStream_t st) { return 
 // those tiles share the stacked C slices; nao even keeps a pair inside one
 // auxiliary block, so both CTAs run the same slice count).  X lands as
 // [(P, mu)][i] either way.
-bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb, bool allow_swap) {
+bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb, int swap) {
   const int nao = c->nao, naux = c->naux;
   const long long c_plane = (long long)c->nocc_max * c->ld_nao;
-  const bool swapped = allow_swap && c->pair_mode >= 1 && nocc <= kTile && (nao & 1) == 0;
+  const bool swapped =
+      nocc <= kTile && ((swap == 1 && c->pair_mode >= 1 && (nao & 1) == 0) || swap == 2);
   if (swapped) {
     if (!make_tmap_bf16(&ta, c->Bd, nao, (long long)naux * nao, c->s_max, c->ld_nao,
                         (long long)naux * nao * c->ld_nao))

@@ -48,9 +48,11 @@ namespace df {
 // the stream when they did; not allowed during stream capture).
 df_status ctx_upload_slices(df_ctx *c, const int *sb, cudaStream_t st);
 // Parameters and operand maps of the two exchange GEMMs of a context.
-// allow_swap: the (P, mu)-rows-on-M layout may be chosen (single-problem
-// launches; the grouped launch runs every problem in the orbitals-on-M one).
-bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb, bool allow_swap = true);
+// swap: 0 orbitals on the MMA's M side; 1 (single problem) the (P, mu)-rows-
+// on-M layout when CTA pairs are on, nocc <= 128 and nao is even; 2 (grouped,
+// one slice count per problem, so a pair may straddle two blocks) that layout
+// whenever nocc <= 128.
+bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb, int swap = 1);
 bool gemm2_setup(df_ctx *c, int nocc, int nsplit, SgParams &q2, CUtensorMap &tx);
 long long xdigit_ld(int nocc);
 }  // namespace df

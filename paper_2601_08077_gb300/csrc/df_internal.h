@@ -106,7 +106,10 @@ bool make_tmap_bf16(CUtensorMap *map, const void *base, long long k, long long r
 cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb,
                               cudaStream_t st);
 // Grouped launch; `mode` is shared by all problems, `grid` CTAs (0 = one per SM).
-cudaError_t launch_slice_gemm_grouped(int mode, const SgGroup &g, int *status, int grid, cudaStream_t st);
+// pairs: CTA-pair launch over tile pairs (kModeXs only; unit_off and total
+// count tile pairs, every problem's npairs set).
+cudaError_t launch_slice_gemm_grouped(int mode, const SgGroup &g, int *status, int grid, cudaStream_t st,
+                                      bool pairs = false);
 int slice_gemm_grid(int nunits);
 int fixed_point_shift(int s, long long k);
 

@@ -852,10 +852,12 @@ cudaError_t launch_mode(const SgParams &p, const CUtensorMap &ta, const CUtensor
 }
 
 // CTA-pair launch: clusters of two CTAs, as many clusters as fit at once
-// (at most one per tile pair), persistent over the tile pairs.
-template <int kMode>
-cudaError_t launch_pair(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
-  auto kern = slice_gemm_kernel<kMode, false, true>;
+// (at most one per tile pair), persistent over the tile pairs; grouped: the
+// tile pairs of several problems (g.total pairs, prefix table in pairs).
+template <int kMode, bool kGrouped = false>
+cudaError_t launch_pair(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st,
+                        const SgGroup *grp = nullptr) {
+  auto kern = slice_gemm_kernel<kMode, kGrouped, true>;
   static int max_clusters = 0;
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
@@ -880,10 +882,12 @@ cudaError_t launch_pair(const SgParams &p, const CUtensorMap &ta, const CUtensor
     }
     max_clusters = n > 0 ? n : 1;
   }
-  const int nc = p.npairs < max_clusters ? p.npairs : max_clusters;
+  const int np = kGrouped ? grp->total : p.npairs;
+  const int nc = np < max_clusters ? np : max_clusters;
   cfg.gridDim = dim3(2 * (unsigned)nc, 1, 1);
   SgGroup g;
   std::memset(&g, 0, sizeof(g));
+  if (kGrouped) g = *grp;
   cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, p, g);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -931,13 +935,18 @@ cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CU
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_slice_gemm_grouped(int mode, const SgGroup &g, int *status, int grid, cudaStream_t st) {
+cudaError_t launch_slice_gemm_grouped(int mode, const SgGroup &g, int *status, int grid, cudaStream_t st,
+                                      bool pairs) {
   if (g.total <= 0) return cudaSuccess;
   SgParams p;
   std::memset(&p, 0, sizeof(p));
   p.status = status;
   CUtensorMap dummy;
   std::memset(&dummy, 0, sizeof(dummy));
+  if (pairs) {
+    if (mode == kModeXs) return launch_pair<kModeXs, true>(p, dummy, dummy, st, &g);
+    return cudaErrorInvalidValue;
+  }
   const int full_grid = slice_gemm_grid(g.total);
   const int gsz = grid > 0 && grid < full_grid ? grid : full_grid;
   switch (mode) {
