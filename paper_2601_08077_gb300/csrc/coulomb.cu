@@ -48,15 +48,22 @@ __global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, 
   }
 }
 
-// Thread per (mu, nu >= mu): J_mn = sum_P B_Pmn rho_P, written to both halves.
+// J_mn = sum_P B_Pmn rho_P over the upper triangle, written to both halves.
+// CTA (x, y) takes elements x*256 .. of the row pair (y, nao-1-y): row y from
+// column y, then row nao-1-y from its diagonal (nao + 1 elements per pair, one
+// row alone in the middle when nao is odd), so every CTA has the same work.
+// Each element's sum runs over P in ascending order, one FMA per P.
 __global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__ B, const double *__restrict__ rho,
                                                       int naux, int nao, double *__restrict__ J) {
   extern __shared__ double srho[];
   for (int i = threadIdx.x; i < naux; i += blockDim.x) srho[i] = rho[i];
   __syncthreads();
-  const int mu = blockIdx.y;
-  const int nu = mu + blockIdx.x * blockDim.x + threadIdx.x;
-  if (nu >= nao) return;
+  const int m0 = blockIdx.y, m1 = nao - 1 - m0;
+  const int len0 = nao - m0, len1 = m1 > m0 ? nao - m1 : 0;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len0 + len1) return;
+  const int mu = e < len0 ? m0 : m1;
+  const int nu = e < len0 ? m0 + e : m1 + (e - len0);
   const long long off = (long long)mu * nao + nu;
   const long long stride = (long long)nao * nao;
   double acc = 0.0;
@@ -72,7 +79,7 @@ __global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__
     acc = fma(b3, srho[P + 3], acc);
   }
   for (; P < naux; ++P) acc = fma(__ldg(B + P * stride + off), srho[P], acc);
-  J[(long long)mu * nao + nu] = acc;
+  J[off] = acc;
   J[(long long)nu * nao + mu] = acc;
 }
 
@@ -141,7 +148,7 @@ cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao
     if (e != cudaSuccess) return e;
     attr = sm;
   }
-  dim3 grid((nao + 255) / 256, nao);
+  dim3 grid((nao + 1 + 255) / 256, (nao + 1) / 2);
   coulomb_kernel<<<grid, 256, sm, st>>>(B, rho, naux, nao, J);
   return cudaGetLastError();
 }
