@@ -346,14 +346,29 @@ df_status df_create(df_ctx **out, int nao, int naux, int nocc_max, int s_max) {
   if (e == cudaSuccess) e = alloc(c, &c->Xd, (size_t)s_max * c->nblk * nao * c->kb_ld_max);
   if (e == cudaSuccess) e = alloc(c, &c->eX, (size_t)c->nblk * nao);
   {
-    // split the K range of each block so the second GEMM has >= 3 work units per SM
+    // split the K range of each block so that the second GEMM's units fill
+    // whole waves of the persistent grid: the smallest split (fewest partials)
+    // with at least one wave and a last wave >= 96 % full, else the fullest
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int nt = (nao + df::kTile - 1) / df::kTile;
     const long long units = (long long)nt * (nt + 1) / 2 * c->nblk;
-    long long ns = (3LL * nsm + units - 1) / units;
-    c->nsplit = (int)(ns < 1 ? 1 : (ns > 8 ? 8 : ns));
+    int best = 1;
+    double best_eff = -1.0;
+    for (int ns = 1; ns <= 8; ++ns) {
+      const double waves = (double)(units * ns) / nsm;
+      const double eff = waves < 1.0 ? waves : waves / std::ceil(waves);
+      if (eff >= 0.96) {
+        best = ns;
+        break;
+      }
+      if (eff > best_eff + 1e-9) {
+        best_eff = eff;
+        best = ns;
+      }
+    }
+    c->nsplit = best;
   }
   if (e == cudaSuccess) e = alloc(c, &c->Rp, (size_t)c->nblk * c->nsplit * nao * nao);
   if (e == cudaSuccess) e = alloc(c, &c->rho, (size_t)naux);
