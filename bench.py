@@ -368,7 +368,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    from paper_2601_08077_gb300 import build, df, inputs
+    from paper_2601_08077_gb300 import build, df, inputs, shard
     if rank == 0 or world == 1:
         build.build_all()
     if world > 1:
@@ -437,10 +437,7 @@ def main():
     ctx.set_profiling(False)
     phases = ctx.phase_times()
     ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(ms, dev)
     ctx.sync_status()
 
     # native FP64 exchange build, same GPU, same B (the comparison build)
