@@ -16,7 +16,7 @@ step time.  The default workload is the 240-atom molecule (nao 1200, naux
 between steps.
 
 Usage: python bench.py [--gpus N --steps K --warmup W --impl ours|reference
-                        --workload large|medium|profile|small|batch|sequence|predictor
+                        --workload large|medium|profile|small|batch|sequence|predictor|scf
                         --nslices S --aux-blocks N --cluster-pairs 0|1|2]
 """
 from __future__ import annotations
@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["small", "profile", "medium", "large", "batch", "sequence", "predictor"],
+    ap.add_argument("--workload", choices=["small", "profile", "medium", "large", "batch", "sequence", "predictor", "scf"],
                     default="large")
     ap.add_argument("--size", choices=["small", "profile", "medium", "large"], default="medium",
                     help="molecule of the sequence / predictor evaluation")
@@ -340,14 +340,51 @@ def run_predictor(args):
             "levels": [r["level"] for r in recs]}
 
 
+def run_scf(args):
+    """RHF to convergence on the neutral He cluster of the chosen size, the
+    exchange precision chosen by the Table 1 rule (level 0 in FP64, and level 0
+    as 8 slices), against the same SCF with every K in native FP64."""
+    import torch
+    from paper_2601_08077_gb300 import build, df, inputs, scf
+    build.build_all()
+    torch.cuda.set_device(0)
+    w = workload(args.size)
+    mol = inputs.molecule(w.n_atoms, w.seed)
+    Z = inputs.nuclear_charges(mol)
+    S, T, V, En = inputs.one_electron(mol, Z)
+    h = T + V
+    nocc = mol.n_atoms
+    ctx = df.Context(mol.nao, mol.naux, nocc)
+    ctx.setup(inputs.df_tensor_device(mol))
+    runs = {}
+    for name, kw in (("fp64", {"mode": "fp64"}), ("rule", {"mode": "rule"}),
+                     ("rule_level0_8_slices", {"mode": "rule", "level0_slices": 8})):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = scf.run(ctx, h, S, nocc, En, **kw)
+        wall = time.perf_counter() - t0
+        its = res["iterations"]
+        runs[name] = {"E": res["E"], "converged": res["converged"], "iterations": len(its),
+                      "ms_jk_total": sum(r["ms"] for r in its), "s_wall": wall,
+                      "levels": [r["level"] for r in its], "slices": [r["slices"] for r in its]}
+    ref = runs["fp64"]
+    for name in ("rule", "rule_level0_8_slices"):
+        r = runs[name]
+        r["dE_vs_fp64_scf"] = r["E"] - ref["E"]
+        r["jk_speedup_vs_fp64"] = ref["ms_jk_total"] / r["ms_jk_total"]
+    return {"metric": "RHF to convergence with DF J/K, exchange precision by the Table 1 rule vs native FP64",
+            "workload": "scf-" + w.name, "nuclear_charge": 2.0, "nocc": nocc, "E_nuc": En, **runs}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload in ("batch", "sequence", "predictor"):
+    if args.workload in ("batch", "sequence", "predictor", "scf"):
         if rank == 0:
-            fn = {"batch": run_batch, "sequence": run_sequence, "predictor": run_predictor}[args.workload]
+            fn = {"batch": run_batch, "sequence": run_sequence, "predictor": run_predictor,
+                  "scf": run_scf}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     w = workload(args.workload)

@@ -115,7 +115,7 @@ df_status df_build_K(df_ctx *ctx, const double *C_dev, int nocc, int nslices, do
 df_status df_build_K_blocks(df_ctx *ctx, const double *C_dev, int nocc, const int *slices_per_block,
                             double *K_dev, df_kstats *stats, void *stream);
 
-/* Energies (the benchmark spec's E_J and E_K, FP64 reductions on the device):
+/* Energies (the Coulomb and exchange energies E_J and E_K of Section 3.2, FP64 reductions on the device):
  * E_host[0] = 1/2 tr(D J), E_host[1] = 1/2 rho.rho (second route to E_J),
  * E_host[2] = -1/2 tr(D K).  Synchronises `stream`; rho_dev may be NULL
  * (then the buffer of the last df_build_J is used). */

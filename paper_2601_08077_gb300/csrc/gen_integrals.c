@@ -94,3 +94,40 @@ void gen_metric(int naux, const double *aux_xyz, const double *aux_exp, double *
     }
   }
 }
+
+/* One-electron integrals over the AO primitives, for an SCF loop around the
+ * build: overlap S, kinetic energy T and attraction V to nuclei of charge
+ * Z[C] at nuc_xyz[C] (all [nao][nao], row-major):
+ *   S_ab = N_a N_b (pi/p)^{3/2} K_ab
+ *   T_ab = (ab/p) (3 - 2 (ab/p) |A-B|^2) S_ab
+ *   V_ab = -sum_C Z_C N_a N_b (2 pi/p) K_ab F0(p |P-C|^2)                  */
+void gen_oneel(int nao, const double *ao_xyz, const double *ao_exp, int nnuc, const double *nuc_xyz,
+               const double *Z, double *S, double *T, double *V) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int a = 0; a < nao; ++a) {
+    const double ea = ao_exp[a];
+    for (int b = 0; b <= a; ++b) {
+      const double eb = ao_exp[b];
+      const double p = ea + eb, mu = ea * eb / p;
+      const double dx = ao_xyz[3 * a] - ao_xyz[3 * b];
+      const double dy = ao_xyz[3 * a + 1] - ao_xyz[3 * b + 1];
+      const double dz = ao_xyz[3 * a + 2] - ao_xyz[3 * b + 2];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double nk = norm_s(ea) * norm_s(eb) * exp(-mu * r2);
+      const double s = nk * pow(kPi / p, 1.5);
+      const double t = mu * (3.0 - 2.0 * mu * r2) * s;
+      const double px = (ea * ao_xyz[3 * a] + eb * ao_xyz[3 * b]) / p;
+      const double py = (ea * ao_xyz[3 * a + 1] + eb * ao_xyz[3 * b + 1]) / p;
+      const double pz = (ea * ao_xyz[3 * a + 2] + eb * ao_xyz[3 * b + 2]) / p;
+      double v = 0.0;
+      for (int c = 0; c < nnuc; ++c) {
+        const double cx = px - nuc_xyz[3 * c], cy = py - nuc_xyz[3 * c + 1], cz = pz - nuc_xyz[3 * c + 2];
+        v -= Z[c] * boys0(p * (cx * cx + cy * cy + cz * cz));
+      }
+      v *= nk * 2.0 * kPi / p;
+      S[(size_t)a * nao + b] = S[(size_t)b * nao + a] = s;
+      T[(size_t)a * nao + b] = T[(size_t)b * nao + a] = t;
+      V[(size_t)a * nao + b] = V[(size_t)b * nao + a] = v;
+    }
+  }
+}

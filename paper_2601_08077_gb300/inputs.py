@@ -64,6 +64,7 @@ def _genlib():
         dp = ctypes.POINTER(ctypes.c_double)
         _lib.gen_int3c.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp]
         _lib.gen_metric.argtypes = [ctypes.c_int, dp, dp, dp]
+        _lib.gen_oneel.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, dp, dp, dp, dp]
     return _lib
 
 
@@ -131,6 +132,25 @@ def metric(mol: Molecule) -> np.ndarray:
     out = np.empty((mol.naux, mol.naux))
     _genlib().gen_metric(mol.naux, _ptr(mol.aux_xyz), _ptr(mol.aux_exp), _ptr(out))
     return out
+
+
+def nuclear_charges(mol: Molecule, Z: float = 2.0) -> np.ndarray:
+    """Charge Z on every atom (2: a closed-shell He-like cluster, nocc = n_atoms)."""
+    return np.full(mol.n_atoms, float(Z))
+
+
+def one_electron(mol: Molecule, Z: np.ndarray):
+    """Overlap S, kinetic T and nuclear attraction V over the AO primitives
+    (for an SCF loop around the build) and the nuclear repulsion energy."""
+    n = mol.nao
+    S, T, V = np.empty((n, n)), np.empty((n, n)), np.empty((n, n))
+    Zc = np.ascontiguousarray(Z, dtype=np.float64)
+    _genlib().gen_oneel(n, _ptr(mol.ao_xyz), _ptr(mol.ao_exp), mol.n_atoms, _ptr(mol.xyz), _ptr(Zc),
+                        _ptr(S), _ptr(T), _ptr(V))
+    R = np.sqrt(np.sum((mol.xyz[:, None, :] - mol.xyz[None, :, :]) ** 2, axis=-1))
+    iu = np.triu_indices(mol.n_atoms, 1)
+    E_nuc = float(np.sum(Zc[iu[0]] * Zc[iu[1]] / R[iu]))
+    return S, T, V, E_nuc
 
 
 def df_tensor(mol: Molecule) -> np.ndarray:

@@ -3,7 +3,7 @@
 Integer work (digits, exponents, slice-pair products) must be bit-exact.
 FP64 results must be bit-exact where the fixed-point recombination is exact
 (truncation T = 0), and otherwise within the bound of the dropped bits; the
-J/K builds must meet the benchmark spec's tolerances max|dK| <= 1e-10 max|K| and
+J/K builds must meet the target tolerances max|dK| <= 1e-10 max|K| and
 |dE| <= 1e-9 Eh at the full slice count.
 """
 import math

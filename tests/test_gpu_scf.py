@@ -1,0 +1,56 @@
+"""RHF on the GPU (cuSOLVER eigensolver, libdf J and K) against the CPU
+oracle's SCF on the same synthetic He cluster: the same converged energy in
+native FP64 and with the exchange precision chosen by Table 1's rule."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import scf_oracle as SO
+from paper_2601_08077_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def system():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_08077_gb300 import build, df
+    build.build_all()
+    mol, B, _, _ = inputs.make_inputs(inputs.SMALL)
+    Z = inputs.nuclear_charges(mol)
+    S, T, V, En = inputs.one_electron(mol, Z)
+    h = T + V
+    ref = SO.scf(h, S, mol.n_atoms, SO.df_jk(B), En)
+    assert ref["converged"]
+    ctx = df.Context(mol.nao, mol.naux, mol.n_atoms)
+    ctx.setup(torch.from_numpy(B).cuda())
+    return df, ctx, h, S, En, mol.n_atoms, ref
+
+
+def _run(system, **kw):
+    from paper_2601_08077_gb300 import scf
+    df, ctx, h, S, En, nocc, ref = system
+    res = scf.run(ctx, h, S, nocc, En, **kw)
+    assert res["converged"]
+    return res, ref, df
+
+
+def test_scf_fp64_matches_oracle(system):
+    res, ref, _ = _run(system, mode="fp64")
+    assert abs(res["E"] - ref["E"]) < 1e-9
+    assert all(r["slices"] == 0 for r in res["iterations"])
+
+
+@pytest.mark.parametrize("level0_slices", [0, 8])
+def test_scf_adaptive_rule_matches_oracle(system, level0_slices):
+    res, ref, df = _run(system, mode="rule", level0_slices=level0_slices)
+    assert abs(res["E"] - ref["E"]) < 1e-9
+    its = res["iterations"]
+    levels = [r["level"] for r in its]
+    assert levels[0] == 4 and levels[1] == 4                  # the rule starts at its coarsest level
+    assert all(a >= b for a, b in zip(levels, levels[1:]))    # and never returns to fewer slices
+    assert its[0]["slices"] == df.level_slices(4)
+    assert its[-1]["level"] <= 1                             # converged at 6 slices or finer
+    assert all(r["slices"] == level0_slices for r in its if r["level"] == 0)
+    assert len(its) <= len(ref["history"]) + 4
