@@ -16,7 +16,7 @@ step time.  The default workload is the 240-atom molecule (nao 1200, naux
 between steps.
 
 Usage: python bench.py [--gpus N --steps K --warmup W --impl ours|reference
-                        --workload large|medium|profile|small|batch|sequence|predictor|scf
+                        --workload large|medium|profile|small|batch|sequence|predictor|scf|crt
                         --nslices S --aux-blocks N --cluster-pairs 0|1|2]
 """
 from __future__ import annotations
@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["small", "profile", "medium", "large", "batch", "sequence", "predictor", "scf"],
+    ap.add_argument("--workload", choices=["small", "profile", "medium", "large", "batch", "sequence", "predictor", "scf",
+                                                   "crt"],
                     default="large")
     ap.add_argument("--size", choices=["small", "profile", "medium", "large"], default="medium",
                     help="molecule of the sequence / predictor evaluation")
@@ -343,7 +344,8 @@ def run_predictor(args):
 def run_scf(args):
     """RHF to convergence on the neutral He cluster of the chosen size, the
     exchange precision chosen by the Table 1 rule (level 0 in FP64, and level 0
-    as 8 slices), against the same SCF with every K in native FP64."""
+    as 8 slices), against the same SCF with every K in native FP64, and with
+    every K at level 4's 3 slices (whose energy error floor the rule avoids)."""
     import torch
     from paper_2601_08077_gb300 import build, df, inputs, scf
     build.build_all()
@@ -358,7 +360,8 @@ def run_scf(args):
     ctx.setup(inputs.df_tensor_device(mol))
     runs = {}
     for name, kw in (("fp64", {"mode": "fp64"}), ("rule", {"mode": "rule"}),
-                     ("rule_level0_8_slices", {"mode": "rule", "level0_slices": 8})):
+                     ("rule_level0_8_slices", {"mode": "rule", "level0_slices": 8}),
+                     ("fixed_3_slices", {"mode": "fixed", "fixed_slices": 3})):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = scf.run(ctx, h, S, nocc, En, **kw)
@@ -368,7 +371,7 @@ def run_scf(args):
                       "ms_jk_total": sum(r["ms"] for r in its), "s_wall": wall,
                       "levels": [r["level"] for r in its], "slices": [r["slices"] for r in its]}
     ref = runs["fp64"]
-    for name in ("rule", "rule_level0_8_slices"):
+    for name in ("rule", "rule_level0_8_slices", "fixed_3_slices"):
         r = runs[name]
         r["dE_vs_fp64_scf"] = r["E"] - ref["E"]
         r["jk_speedup_vs_fp64"] = ref["ms_jk_total"] / r["ms_jk_total"]
@@ -376,15 +379,74 @@ def run_scf(args):
             "workload": "scf-" + w.name, "nuclear_charge": 2.0, "nocc": nocc, "E_nuc": En, **runs}
 
 
+def run_crt(args):
+    """The two exchange contractions of the chosen molecule (X = B C over rows
+    (P, mu), and one block's K_b = X_b X_b^T) emulated by INT8 slices and by
+    the CRT variant (Ozaki scheme II) at each Table 1 level (the CRT modulus
+    count resolving rows like the level's slices), against cuBLAS DGEMM:
+    per-call time (split, tensor-core GEMMs, recombination or reconstruction;
+    scratch from a warm pool) and error relative to max|DGEMM|."""
+    import torch
+    from paper_2601_08077_gb300 import build, df, inputs
+    build.build_all()
+    torch.cuda.set_device(0)
+    w = workload(args.size)
+    mol = inputs.molecule(w.n_atoms, w.seed)
+    Bt = inputs.df_tensor_device(mol)
+    nao, nocc = mol.nao, w.nocc
+    C = torch.from_numpy(inputs.orbitals(nao, nocc, w.seed + 1)).cuda()
+    A1 = Bt.reshape(-1, nao)
+    B1 = C.T.contiguous()
+    Xb = (A1[:128 * nao] @ C).reshape(128, nao, nocc)
+    A2 = Xb.permute(1, 0, 2).reshape(nao, -1).contiguous()
+
+    def timed(fn, reps=5, warm=2):
+        for _ in range(warm):
+            out = fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), out
+
+    shapes = {}
+    for name, A, B in (("X=BC", A1, B1), ("K_b=X_bX_b^T", A2, A2)):
+        M, K = A.shape
+        N = B.shape[0]
+        flops = 2.0 * M * N * K
+        t64, ref = timed(lambda: A @ B.T)
+        scale = float(ref.abs().max())
+        rows = []
+        for s in (3, 4, 5, 6, 7):
+            n = df.crt_moduli_for_bits(K, 8 * s - 1)
+            ts, o_s = timed(lambda: df.emulated_gemm(A, B, s))
+            tc, o_c = timed(lambda: df.emulated_gemm_crt(A, B, n))
+            rows.append({"slices": s, "slice_products": s * (s + 1) // 2, "ms_slices": ts,
+                         "err_slices": float((o_s - ref).abs().max()) / scale,
+                         "moduli": n, "q": df.crt_operand_bits(K, n), "ms_crt": tc,
+                         "err_crt": float((o_c - ref).abs().max()) / scale,
+                         "tflops_slices": flops / ts / 1e9, "tflops_crt": flops / tc / 1e9})
+            del o_s, o_c
+        shapes[name] = {"M": M, "N": N, "K": K, "ms_dgemm": t64, "tflops_dgemm": flops / t64 / 1e9,
+                        "levels": rows}
+    return {"metric": "emulated FP64 GEMM, INT8 slices vs CRT (Ozaki scheme II), per Table 1 level",
+            "workload": w.name, "shapes": shapes}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload in ("batch", "sequence", "predictor", "scf"):
+    if args.workload in ("batch", "sequence", "predictor", "scf", "crt"):
         if rank == 0:
             fn = {"batch": run_batch, "sequence": run_sequence, "predictor": run_predictor,
-                  "scf": run_scf}[args.workload]
+                  "scf": run_scf, "crt": run_crt}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     w = workload(args.workload)

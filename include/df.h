@@ -155,6 +155,49 @@ df_status df_emulated_gemm(const double *A_dev, const double *B_dev, int M, int 
 df_status df_emulated_gemm_static(const double *A_dev, const double *B_dev, int M, int N, int K, int nslices,
                                   double *out_dev, void *stream);
 
+/* CRT variant of the emulated GEMM: Ozaki scheme II (Ozaki, Uchino and
+ * Imamura, 2025), the other INT8 emulation Section 2.3 names, computed on the
+ * same tensor-core slice GEMM.  Moduli: the integers <= 256 taken greedily
+ * downwards, each coprime to the ones before (256, 255, 253, 251, 247, ...),
+ * at most DF_CRT_MAX_MODULI.  For K-term sums with n moduli (product M_n) the
+ * operands are scaled per row to integers A' = RNE(A 2^(q-1-e)) (e the
+ * smallest integer with max|row| < 127/128 2^e) with q the largest width
+ * <= 63 such that K 2^(2q-1) < M_n; the exact integer product is rebuilt from
+ * its residues by the Chinese remainder theorem and rounded once to FP64. */
+#define DF_CRT_MAX_MODULI 16
+
+/* The i-th modulus (0-based); 0 if i is out of range.  Host only. */
+int df_crt_modulus(int i);
+
+/* The operand width q for K-term sums with nmod moduli; 0 if K is outside
+ * [1, 2^26] or nmod outside [2, 16] or no width >= 2 fits.  Host only. */
+int df_crt_operand_bits(long long K, int nmod);
+
+/* The fewest moduli whose width q reaches bits + 1, i.e. the resolution of
+ * Table 1's level with m_emu = bits (s = (bits + 1) / 8 slices resolve a row
+ * to 2^(e - 8s)); 0 if 16 moduli do not reach it.  Host only. */
+int df_crt_moduli_for_bits(long long K, int bits);
+
+/* Inspection entry point: exps_dev [rows] (int32) and the centred residues
+ * res_dev [nmod][rows][cols] (int16, in [-floor((m-1)/2), floor(m/2)]) of
+ * A' mod m_i for the rows of A (device [rows][ld]) with K = cols. */
+df_status df_crt_split_rows(const double *A_dev, int rows, int cols, int ld, int nmod, int32_t *exps_dev,
+                            int16_t *res_dev, void *stream);
+
+/* Inspection entry point: y_i = (a_i b_i^T) mod m_i for A (device [M][K]) and
+ * B (device [N][K]), Y_dev [nmod][M][N] (uint8), exponents ea_dev [M], eb_dev
+ * [N] (may be NULL).  Allocates scratch; synchronises `stream`. */
+df_status df_crt_residue_products(const double *A_dev, const double *B_dev, int M, int N, int K, int nmod,
+                                  uint8_t *Y_dev, int32_t *ea_dev, int32_t *eb_dev, void *stream);
+
+/* out = A B^T (A [M][K], B [N][K], out [M][N], all device, row-major)
+ * emulated with nmod moduli; K <= 2^26.  Allocates scratch (2 nmod (M + N)
+ * round_up(K, 8) bytes of residue planes, nmod M round_up(N, 16) bytes of
+ * residue products); synchronises `stream`.  DF_ERR_ARG for sizes or a
+ * modulus count that admit no width q >= 2. */
+df_status df_emulated_gemm_crt(const double *A_dev, const double *B_dev, int M, int N, int K, int nmod,
+                               double *out_dev, void *stream);
+
 /* Table 1 (Section 3.2): the emulation level for the next iteration given the
  * relative energy change (>= lower bound of the row); level 0 = FP64. */
 int df_level_for(double dE_rel);

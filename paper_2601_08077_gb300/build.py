@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdf.so")
-CU_SOURCES = ["split.cu", "slicegemm.cu", "coulomb.cu", "df_api.cu", "noalloc.cu", "batch.cu", "mlp.cu", "cderi.cu"]
+CU_SOURCES = ["split.cu", "slicegemm.cu", "coulomb.cu", "df_api.cu", "noalloc.cu", "batch.cu", "mlp.cu", "cderi.cu", "crt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

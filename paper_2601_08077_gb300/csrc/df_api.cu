@@ -613,11 +613,11 @@ df_status grid_gemm(const double *A, const double *B, int M, int N, int K, int s
   uint16_t *Ad = nullptr, *Bd = nullptr;
   int *ea = nullptr, *eb = nullptr, *status = nullptr;
   df_status rs = DF_OK;
-  cudaError_t e = cudaMalloc(&Ad, sizeof(uint16_t) * (size_t)s * M * ld);
-  if (e == cudaSuccess) e = cudaMalloc(&Bd, sizeof(uint16_t) * (size_t)s * N * ld);
-  if (e == cudaSuccess) e = cudaMalloc(&ea, sizeof(int) * M);
-  if (e == cudaSuccess) e = cudaMalloc(&eb, sizeof(int) * N);
-  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  cudaError_t e = df::scratch_malloc((void **)&Ad, sizeof(uint16_t) * (size_t)s * M * ld, st);
+  if (e == cudaSuccess) e = df::scratch_malloc((void **)&Bd, sizeof(uint16_t) * (size_t)s * N * ld, st);
+  if (e == cudaSuccess) e = df::scratch_malloc((void **)&ea, sizeof(int) * M, st);
+  if (e == cudaSuccess) e = df::scratch_malloc((void **)&eb, sizeof(int) * N, st);
+  if (e == cudaSuccess) e = df::scratch_malloc((void **)&status, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
   // raw mode adds every chunk into its group's output: start from zero
   if (e == cudaSuccess && mode == df::kModeRaw) e = cudaMemsetAsync(raw, 0, sizeof(int64_t) * (size_t)s * M * N, st);
@@ -654,13 +654,10 @@ df_status grid_gemm(const double *A, const double *B, int M, int N, int K, int s
   if (e == cudaSuccess && rs == DF_OK) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && rs == DF_OK && ea_out) e = cudaMemcpyAsync(ea_out, ea, sizeof(int) * M, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && rs == DF_OK && eb_out) e = cudaMemcpyAsync(eb_out, eb, sizeof(int) * N, cudaMemcpyDeviceToDevice, st);
+  for (void *ptr : {(void *)Ad, (void *)Bd, (void *)ea, (void *)eb, (void *)status})
+    if (ptr) cudaFreeAsync(ptr, st);
   cudaError_t es = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = es;
-  cudaFree(Ad);
-  cudaFree(Bd);
-  cudaFree(ea);
-  cudaFree(eb);
-  cudaFree(status);
   if (rs != DF_OK) return rs;
   if (e != cudaSuccess) return DF_ERR_CUDA;
   return h ? DF_ERR_TIMEOUT : DF_OK;

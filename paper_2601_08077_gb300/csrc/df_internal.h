@@ -25,6 +25,8 @@ enum SgMode : int {
   kModeGemm = 3,    // generic emulated product: out[m*ld + n]
   kModeXs = 4,      // first exchange GEMM with swapped operands (rows (P, mu) on the A side):
                     // int64 sums R[m*ld + n], the same X layout as kModeX
+  kModeMod = 5,     // CRT variant: the exact sum of one modulus plane reduced modulo that
+                    // modulus, one byte each: out8[plane*out_blk + m*ld + n]
 };
 
 // How the persistent kernel turns a unit index into a tile.
@@ -33,7 +35,10 @@ enum SgLayout : int {
   kLayoutX = 1,      // first exchange GEMM: n rows are (P, mu); block = n0 / (128 nao)
   kLayoutKPart = 2,  // second exchange GEMM: u -> (upper tile pair, block)
   kLayoutXs = 3,     // first exchange GEMM, swapped: m rows are (P, mu); block = m0 / (128 nao)
+  kLayoutCrt = 4,    // CRT variant: u -> (plane = u / (nt_m nt_n), grid tile), planes az = bz = plane
 };
+
+constexpr int kCrtMaxModuli = 16;
 
 struct SgParams {
   int layout, mode;
@@ -58,6 +63,7 @@ struct SgParams {
   // Work is then counted in tile pairs (npairs); the host sets both.
   int pair;
   int npairs;
+  int crt_mod[kCrtMaxModuli];  // kModeMod: the modulus of each plane
 };
 
 // Tile pairs of a launch in CTA-pair mode (0 = the layout has no pairing):
@@ -78,6 +84,24 @@ struct SgGroup {
 };
 
 struct Ctx;
+
+// Scratch of the stand-alone emulated-GEMM entry points: stream-ordered
+// allocations from the device's default pool, whose release threshold is
+// raised once so that repeated calls reuse the memory instead of mapping it
+// again (it stays reserved by the process until cudaDeviceReset).
+inline cudaError_t scratch_malloc(void **p, size_t bytes, cudaStream_t st) {
+  static bool kept[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !kept[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    kept[dev] = true;
+  }
+  return cudaMallocAsync(p, bytes, st);
+}
 
 // Kernel launchers (split.cu, slicegemm.cu, coulomb.cu).
 cudaError_t launch_split_rows_bf16(const double *A, long long rows, int cols, long long ld, int nslices,

@@ -315,6 +315,16 @@ __device__ __forceinline__ Unit grid_unit(const SgParams &p, int mt, int nt) {
 
 __device__ __forceinline__ Unit decode_unit(const SgParams &p, int u) {
   Unit w;
+  if (p.layout == kLayoutCrt) {
+    // plane-major, so the B tile of a plane is reused from L2 by its m tiles
+    const int per = p.nt_m * p.nt_n;
+    const int plane = u / per, r = u % per;
+    w = grid_unit(p, r % p.nt_m, r / p.nt_m);
+    w.az0 = plane;
+    w.bz0 = plane;
+    w.blk = plane;
+    return w;
+  }
   if (p.layout == kLayoutKPart) {
     // u -> (block b, K split sp, upper tile pair); block-major for L2 reuse
     const int npairs = p.nt_m * (p.nt_m + 1) / 2;
@@ -373,9 +383,52 @@ __device__ __forceinline__ void store64_x(const SgParams &p, int m, int n0c, con
   }
 }
 
+// v mod m in [0, m) for |v| < 2^24 and m >= 3: the FP32 quotient of the exact
+// float(v) is within 1 of v / m, so one correction step suffices.
+__device__ __forceinline__ int mod_small24(int v, int m, float inv) {
+  const int q = __float2int_rd((float)v * inv);
+  int r = v - q * m;
+  if (r < 0)
+    r += m;
+  else if (r >= m)
+    r -= m;
+  return r;
+}
+
+// R mod m in [0, m) for |R| < 2^40: R = a 2^24 + b with |a| < 2^16 and
+// 0 <= b < 2^24, and a 2^24 = a (2^24 mod m) (mod m) with |a c24| < 2^24.
+__device__ __forceinline__ int mod_i40(long long R, int m, float inv, int c24) {
+  const int a = (int)(R >> 24);
+  const int b = (int)(R & 0xFFFFFF);
+  const int r = mod_small24(a * c24, m, inv) + mod_small24(b, m, inv);
+  return r >= m ? r - m : r;
+}
+
 template <int kMode>
 __device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m, int n0c, const long long (&R)[64],
                                         int kexp_base, int ea_m) {
+  if (kMode == kModeMod) {
+    // CRT variant: y = S mod m_plane, one byte per element, row-major per plane
+    if (m >= p.m_valid) return;
+    const int md = p.crt_mod[w.blk];
+    const float inv = 1.0f / (float)md;
+    const int c24 = (int)((1u << 24) % (unsigned)md);
+    uint8_t *out = reinterpret_cast<uint8_t *>(p.out) + (long long)w.blk * p.out_blk + (long long)m * p.out_ld + n0c;
+    if (n0c + 64 <= p.n_valid) {
+#pragma unroll
+      for (int j8 = 0; j8 < 8; ++j8) {
+        uint64_t word = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) word |= (uint64_t)mod_i40(R[8 * j8 + j], md, inv, c24) << (8 * j);
+        reinterpret_cast<uint64_t *>(out)[j8] = word;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 64; ++j)
+        if (n0c + j < p.n_valid) out[j] = (uint8_t)mod_i40(R[j], md, inv, c24);
+    }
+    return;
+  }
   if (kMode == kModeX) {
     store64_x(p, m, n0c, R);
     return;
@@ -931,6 +984,7 @@ cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CU
     case kModeRaw: return launch_mode<kModeRaw, false>(p, ta, tb, g, grid, st);
     case kModeGemm: return launch_mode<kModeGemm, false>(p, ta, tb, g, grid, st);
     case kModeXs: return launch_mode<kModeXs, false>(p, ta, tb, g, grid, st);
+    case kModeMod: return launch_mode<kModeMod, false>(p, ta, tb, g, grid, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -97,6 +97,13 @@ def lib():
         L.df_block_errors.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]
         L.df_workspace_bytes.argtypes = [P]
         L.df_workspace_bytes.restype = ctypes.c_int64
+        LL = ctypes.c_longlong
+        L.df_crt_modulus.argtypes = [I]
+        L.df_crt_operand_bits.argtypes = [LL, I]
+        L.df_crt_moduli_for_bits.argtypes = [LL, I]
+        L.df_crt_split_rows.argtypes = [P, I, I, I, I, P, P, V]
+        L.df_crt_residue_products.argtypes = [P, P, I, I, I, I, P, P, P, V]
+        L.df_emulated_gemm_crt.argtypes = [P, P, I, I, I, I, P, V]
         _lib = L
     return _lib
 
@@ -165,6 +172,50 @@ def emulated_gemm(A: torch.Tensor, B: torch.Tensor, nslices: int, stream=None):
     out = torch.empty((M, N), dtype=torch.float64, device=A.device)
     _check(lib().df_emulated_gemm(_f64(A), _f64(B), M, N, K, nslices, _ptr(out), _stream(stream)),
            "df_emulated_gemm")
+    return out
+
+
+def crt_modulus(i: int) -> int:
+    return lib().df_crt_modulus(int(i))
+
+
+def crt_operand_bits(K: int, nmod: int) -> int:
+    return lib().df_crt_operand_bits(int(K), int(nmod))
+
+
+def crt_moduli_for_bits(K: int, bits: int) -> int:
+    return lib().df_crt_moduli_for_bits(int(K), int(bits))
+
+
+def crt_split_rows(A: torch.Tensor, nmod: int, stream=None):
+    """Row exponents (int32) and centred residues int16 [nmod, rows, cols] of the scaled rows of A."""
+    rows, cols = A.shape
+    exps = torch.empty(rows, dtype=torch.int32, device=A.device)
+    res = torch.empty((nmod, rows, cols), dtype=torch.int16, device=A.device)
+    _check(lib().df_crt_split_rows(_f64(A), rows, cols, cols, nmod, _ptr(exps), _ptr(res), _stream(stream)),
+           "df_crt_split_rows")
+    return exps, res
+
+
+def crt_residue_products(A: torch.Tensor, B: torch.Tensor, nmod: int, stream=None):
+    """y_i = (a_i b_i^T) mod m_i as uint8 [nmod, M, N], plus the row exponents of A and B."""
+    M, K = A.shape
+    N, _ = B.shape
+    Y = torch.empty((nmod, M, N), dtype=torch.uint8, device=A.device)
+    ea = torch.empty(M, dtype=torch.int32, device=A.device)
+    eb = torch.empty(N, dtype=torch.int32, device=A.device)
+    _check(lib().df_crt_residue_products(_f64(A), _f64(B), M, N, K, nmod, _ptr(Y), _ptr(ea), _ptr(eb),
+                                         _stream(stream)), "df_crt_residue_products")
+    return Y, ea, eb
+
+
+def emulated_gemm_crt(A: torch.Tensor, B: torch.Tensor, nmod: int, stream=None):
+    """A @ B^T emulated through the residues of nmod moduli (CRT variant)."""
+    M, K = A.shape
+    N, _ = B.shape
+    out = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    _check(lib().df_emulated_gemm_crt(_f64(A), _f64(B), M, N, K, nmod, _ptr(out), _stream(stream)),
+           "df_emulated_gemm_crt")
     return out
 
 

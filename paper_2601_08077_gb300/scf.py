@@ -39,11 +39,13 @@ def _diis(Fs, errs):
     return torch.einsum("i,ijk->jk", c, torch.stack(Fs))
 
 
-def run(ctx, h, S, nocc: int, E_nuc: float, mode: str = "rule", level0_slices: int = 0, maxiter: int = 60,
-        e_tol: float = 1e-10, d_tol: float = 1e-7, ndiis: int = 8, device="cuda"):
-    """SCF on the context's B.  mode: 'rule' (Table 1) or 'fp64' (every K in
-    FP64).  Returns per-iteration records (level, slices, E, dE, ms of the J/K
-    build and energies) and the final energy."""
+def run(ctx, h, S, nocc: int, E_nuc: float, mode: str = "rule", level0_slices: int = 0, fixed_slices: int = 3,
+        maxiter: int = 60, e_tol: float = 1e-10, d_tol: float = 1e-7, ndiis: int = 8, device="cuda"):
+    """SCF on the context's B.  mode: 'rule' (Table 1), 'fp64' (every K in
+    FP64) or 'fixed' (every K at `fixed_slices`, the fixed-level runs the
+    paper contrasts with the rule in Section 4).  Returns per-iteration
+    records (level, slices, E, dE, ms of the J/K build and energies) and the
+    final energy."""
     dev = torch.device(device)
     h = torch.as_tensor(h, dtype=torch.float64, device=dev)
     S = torch.as_tensor(S, dtype=torch.float64, device=dev)
@@ -65,7 +67,7 @@ def run(ctx, h, S, nocc: int, E_nuc: float, mode: str = "rule", level0_slices: i
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         ctx.build_J(D, J, rho)
-        ns = 0 if mode == "fp64" else s
+        ns = {"fp64": 0, "fixed": fixed_slices}.get(mode, s)
         ctx.build_K(C_occ, ns, K)
         EJ, _, EK = ctx.energy(D, J, K, rho)
         e1.record()

@@ -48,3 +48,19 @@ def test_pure_host_entry_points():
     h = ctypes.c_void_p()
     assert lib.df_create(ctypes.byref(h), 0, 10, 2, 8) == -1      # rejected before any allocation
     assert lib.df_create(ctypes.byref(h), 10, 10, 2, 9) == -1
+
+
+def test_crt_host_entry_points_match_the_oracle():
+    from paper_2601_08077_gb300 import build
+    from oracle import crt_oracle as CO
+    lib = ctypes.CDLL(build.build_library())
+    lib.df_crt_operand_bits.argtypes = [ctypes.c_longlong, ctypes.c_int]
+    lib.df_crt_moduli_for_bits.argtypes = [ctypes.c_longlong, ctypes.c_int]
+    assert [lib.df_crt_modulus(i) for i in range(CO.MAX_MODULI)] == CO.moduli(CO.MAX_MODULI)
+    assert lib.df_crt_modulus(-1) == 0 and lib.df_crt_modulus(CO.MAX_MODULI) == 0
+    for K in (1, 7, 64, 100, 600, 1200, 32000, 2 ** 20, 2 ** 26):
+        for n in range(2, CO.MAX_MODULI + 1):
+            assert lib.df_crt_operand_bits(K, n) == CO.operand_bits(K, n), (K, n)
+        for bits in (23, 31, 39, 47, 52):
+            assert lib.df_crt_moduli_for_bits(K, bits) == CO.moduli_for_bits(K, bits), (K, bits)
+    assert lib.df_crt_operand_bits(2 ** 26 + 1, 8) == 0 and lib.df_crt_operand_bits(10, 17) == 0

@@ -54,3 +54,13 @@ def test_scf_adaptive_rule_matches_oracle(system, level0_slices):
     assert its[-1]["level"] <= 1                             # converged at 6 slices or finer
     assert all(r["slices"] == level0_slices for r in its if r["level"] == 0)
     assert len(its) <= len(ref["history"]) + 4
+
+
+def test_scf_fixed_three_slices_has_an_error_floor(system):
+    # every K at level 4's 3 slices (24 bits) stalls well above the rule's
+    # accuracy: the reason the rule raises the precision as dE falls
+    from paper_2601_08077_gb300 import scf
+    df, ctx, h, S, En, nocc, ref = system
+    res = scf.run(ctx, h, S, nocc, En, mode="fixed", fixed_slices=3, maxiter=40)
+    assert all(r["slices"] == 3 for r in res["iterations"])
+    assert abs(res["E"] - ref["E"]) > 1e-8
