@@ -19,7 +19,7 @@
 // The residues come from the balanced base-256 digits of A' (the digits of the
 // slice scheme): A' = sum_j b_j 256^j with signed bytes b_j, so A' mod m is
 // congruent to two 4-way signed byte dot products (dp4a) with the centred
-// weights 256^j mod m, a sum below 2^17 that one FP32 step reduces.  The
+// weights 256^j mod m, a sum below 2^17 that one Barrett step reduces.  The
 // reconstruction accumulates sum_i y_i W_i (W_i the CRT weights) in 32-bit
 // limbs, estimates the quotient by M in FP32 and finishes in 128-bit integers.
 // No FP64 instruction is used: GB300's FP64 pipe is narrow.
@@ -36,7 +36,8 @@ struct CrtTab {
   int n;                            // moduli
   int q1;                           // q - 1
   int mod[kCrtMaxModuli];
-  float inv[kCrtMaxModuli];         // fl32(1 / m)
+  uint32_t magic[kCrtMaxModuli];    // ceil(2^32 / m)
+  int off17[kCrtMaxModuli];         // a multiple of m >= 2^17
   int wlo[kCrtMaxModuli];           // centred 256^j mod m, j = 0..3, one signed byte each
   int whi[kCrtMaxModuli];           // j = 4..7
   uint32_t W[kCrtMaxModuli][4];     // CRT weights (M/m_i) ((M/m_i)^-1 mod m_i), 32-bit limbs
@@ -99,7 +100,8 @@ bool make_tab(long long K, int n, CrtTab *t) {
   for (int i = 0; i < n; ++i) M *= (u128)t->mod[i];
   for (int i = 0; i < n; ++i) {
     const int m = t->mod[i];
-    t->inv[i] = 1.0f / (float)m;
+    t->magic[i] = (uint32_t)(0xFFFFFFFFu / (uint32_t)m + 1u);
+    t->off17[i] = ((1 << 17) + m - 1) / m * m;
     int lo = 0, hi = 0, w = 1 % m;
     for (int j = 0; j < 8; ++j) {
       const int c = w > m / 2 ? w - m : w;  // centred, in [-128, 127]
@@ -180,22 +182,16 @@ __device__ __forceinline__ long long scaled_rne_q(uint64_t bits, int e, int q1) 
   return (bits >> 63) ? -N : N;
 }
 
-// v mod m in [0, m) for |v| < 2^24 (the FP32 quotient is within 1 of v / m).
-__device__ __forceinline__ int mod24(int v, int m, float inv) {
-  const int q = __float2int_rd((float)v * inv);
-  int r = v - q * m;
-  if (r < 0)
-    r += m;
-  else if (r >= m)
-    r -= m;
-  return r;
-}
-
-// Centred residue of the integer whose balanced digit words are (hi, lo).
+// Centred residue of the integer whose balanced digit words are (hi, lo):
+// S = sum_j b_j (256^j mod m) has |S| <= 8 128^2 = 2^17; S + off17 >= 0 is
+// reduced by a Barrett step (the high word of v ceil(2^32 / m) is floor(v / m)
+// or one more).
 __device__ __forceinline__ int residue(int lo, int hi, const CrtTab &t, int i) {
-  const int S = __dp4a(lo, t.wlo[i], __dp4a(hi, t.whi[i], 0));  // |S| <= 8 128^2
+  const int S = __dp4a(lo, t.wlo[i], __dp4a(hi, t.whi[i], 0));
   const int m = t.mod[i];
-  const int r = mod24(S, m, t.inv[i]);
+  const uint32_t v = (uint32_t)(S + t.off17[i]);
+  int r = (int)(v - __umulhi(v, t.magic[i]) * (uint32_t)m);
+  if (r < 0) r += m;
   return r > (m >> 1) ? r - m : r;
 }
 
@@ -218,28 +214,30 @@ __global__ void __launch_bounds__(256)
   const int e = exponent_from_max_bits_dev(mx);
   if (lane == 0) exps[r] = e;
   uint16_t *drow = planes + r * dld;
-  for (int c = 2 * lane; c < cols; c += 64) {
-    const bool two = c + 1 < cols;
-    int lo[2], hi[2];
+  // four columns per lane per step: four independent chains per residue
+  for (int c = 4 * lane; c < cols; c += 128) {
+    const int nv = cols - c < 4 ? cols - c : 4;
+    int lo[4], hi[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint64_t b = (h == 0 || two) ? (uint64_t)__double_as_longlong(row[c + h]) : 0ull;
+    for (int h = 0; h < 4; ++h) {
+      const uint64_t b = h < nv ? (uint64_t)__double_as_longlong(row[c + h]) : 0ull;
       // balanced digits: byte j of Mg is b_j + 128 for j < 7, the top byte is b_7
       const long long Mg = scaled_rne_q(b, e, t.q1) + 0x0080808080808080ll;
       lo[h] = (int)((uint32_t)Mg ^ 0x80808080u);
       hi[h] = (int)((uint32_t)((unsigned long long)Mg >> 32) ^ 0x00808080u);
     }
     for (int i = 0; i < t.n; ++i) {
-      const int r0 = residue(lo[0], hi[0], t, i);
-      const int r1 = residue(lo[1], hi[1], t, i);
+      uint32_t v[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int rr = residue(lo[h], hi[h], t, i);
+        v[h] = kInspect ? (uint32_t)(uint16_t)(int16_t)rr : (uint32_t)int_to_bf16_bits(rr);
+      }
       uint16_t *dst = drow + (long long)i * pstride + c;
-      const uint32_t pk = kInspect ? ((uint32_t)(uint16_t)(int16_t)r0 | ((uint32_t)(uint16_t)(int16_t)r1 << 16))
-                                   : ((uint32_t)int_to_bf16_bits(r0) | ((uint32_t)int_to_bf16_bits(r1) << 16));
-      if (two && ((reinterpret_cast<uintptr_t>(dst) & 3) == 0)) {
-        *reinterpret_cast<uint32_t *>(dst) = pk;
+      if (nv == 4 && ((reinterpret_cast<uintptr_t>(dst) & 7) == 0)) {
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
       } else {
-        dst[0] = (uint16_t)(pk & 0xFFFF);
-        if (two) dst[1] = (uint16_t)(pk >> 16);
+        for (int h = 0; h < nv; ++h) dst[h] = (uint16_t)v[h];
       }
     }
   }

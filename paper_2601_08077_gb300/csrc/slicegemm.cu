@@ -70,6 +70,12 @@ constexpr uint64_t kTimeoutNs = 4000000000ull;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*alignment slack*/;
 constexpr int kSmemBytesP = kStagesP * kStageBytesP + 1024 /*barriers*/ + 1024 /*alignment slack*/;
 static_assert(kSmemBytesP <= 232448, "pair ring must fit the 227 KB opt-in shared memory of a CTA");
+// CRT variant (kModeMod): one B tile per stage and short units (one plane,
+// K / 64 stages each) streaming a large A operand, so the ring is deepened
+// to keep more DRAM reads in flight.
+constexpr int kStagesM = 7;
+constexpr int kSmemBytesM = kStagesM * kStageBytesP + 1024 /*barriers*/ + 1024 /*alignment slack*/;
+static_assert(kSmemBytesM <= 232448, "CRT ring must fit the 227 KB opt-in shared memory of a CTA");
 // Register split (setmaxnreg): warps 0-3 drop to 56, the 8 epilogue warps rise
 // to 224; 128*56 + 256*224 = 64512 = 384 threads * 168 registers at launch.
 constexpr int kRegsLow = 56;
@@ -383,24 +389,20 @@ __device__ __forceinline__ void store64_x(const SgParams &p, int m, int n0c, con
   }
 }
 
-// v mod m in [0, m) for |v| < 2^24 and m >= 3: the FP32 quotient of the exact
-// float(v) is within 1 of v / m, so one correction step suffices.
-__device__ __forceinline__ int mod_small24(int v, int m, float inv) {
-  const int q = __float2int_rd((float)v * inv);
-  int r = v - q * m;
-  if (r < 0)
-    r += m;
-  else if (r >= m)
-    r -= m;
-  return r;
+// v mod m for 0 <= v < 2^32 and 2 <= m <= 256 with magic = ceil(2^32 / m):
+// the high word of v * magic is floor(v / m) or one more, so one correction.
+__device__ __forceinline__ int umod_barrett(uint32_t v, int m, uint32_t magic) {
+  const int r = (int)(v - __umulhi(v, magic) * (uint32_t)m);
+  return r < 0 ? r + m : r;
 }
 
 // R mod m in [0, m) for |R| < 2^40: R = a 2^24 + b with |a| < 2^16 and
-// 0 <= b < 2^24, and a 2^24 = a (2^24 mod m) (mod m) with |a c24| < 2^24.
-__device__ __forceinline__ int mod_i40(long long R, int m, float inv, int c24) {
+// 0 <= b < 2^24; a 2^24 = a c24 (mod m) with c24 = 2^24 mod m, |a c24| < 2^24,
+// made non-negative by off24, a multiple of m >= 2^24.
+__device__ __forceinline__ int mod_i40(long long R, int m, uint32_t magic, int c24, int off24) {
   const int a = (int)(R >> 24);
-  const int b = (int)(R & 0xFFFFFF);
-  const int r = mod_small24(a * c24, m, inv) + mod_small24(b, m, inv);
+  const uint32_t b = (uint32_t)(R & 0xFFFFFF);
+  const int r = umod_barrett((uint32_t)(a * c24 + off24), m, magic) + umod_barrett(b, m, magic);
   return r >= m ? r - m : r;
 }
 
@@ -411,21 +413,22 @@ __device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m,
     // CRT variant: y = S mod m_plane, one byte per element, row-major per plane
     if (m >= p.m_valid) return;
     const int md = p.crt_mod[w.blk];
-    const float inv = 1.0f / (float)md;
+    const uint32_t magic = 0xFFFFFFFFu / (uint32_t)md + 1u;
     const int c24 = (int)((1u << 24) % (unsigned)md);
+    const int off24 = (int)(((1u << 24) + (unsigned)md - 1u) / (unsigned)md * (unsigned)md);
     uint8_t *out = reinterpret_cast<uint8_t *>(p.out) + (long long)w.blk * p.out_blk + (long long)m * p.out_ld + n0c;
     if (n0c + 64 <= p.n_valid) {
 #pragma unroll
       for (int j8 = 0; j8 < 8; ++j8) {
         uint64_t word = 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) word |= (uint64_t)mod_i40(R[8 * j8 + j], md, inv, c24) << (8 * j);
+        for (int j = 0; j < 8; ++j) word |= (uint64_t)mod_i40(R[8 * j8 + j], md, magic, c24, off24) << (8 * j);
         reinterpret_cast<uint64_t *>(out)[j8] = word;
       }
     } else {
 #pragma unroll
       for (int j = 0; j < 64; ++j)
-        if (n0c + j < p.n_valid) out[j] = (uint8_t)mod_i40(R[j], md, inv, c24);
+        if (n0c + j < p.n_valid) out[j] = (uint8_t)mod_i40(R[j], md, magic, c24, off24);
     }
     return;
   }
@@ -502,8 +505,8 @@ template <int kMode, bool kGrouped, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
                       const SgParams p, const SgGroup grp) {
-  constexpr int NS = kPair ? kStagesP : kStages;
-  constexpr int SB = kPair ? kStageBytesP : kStageBytes;
+  constexpr int NS = kPair ? kStagesP : (kMode == kModeMod ? kStagesM : kStages);
+  constexpr int SB = (kPair || kMode == kModeMod) ? kStageBytesP : kStageBytes;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + NS * SB);
@@ -893,14 +896,15 @@ int slice_gemm_grid(int nunits) {
 template <int kMode, bool kGrouped>
 cudaError_t launch_mode(const SgParams &p, const CUtensorMap &ta, const CUtensorMap &tb, const SgGroup &g, int grid,
                         cudaStream_t st) {
+  constexpr int smem = kMode == kModeMod ? kSmemBytesM : kSmemBytes;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<kMode, kGrouped, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  slice_gemm_kernel<kMode, kGrouped, false><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, p, g);
+  slice_gemm_kernel<kMode, kGrouped, false><<<grid, kThreads, smem, st>>>(ta, tb, p, g);
   return cudaGetLastError();
 }
 
