@@ -357,7 +357,15 @@ def run_scf(args):
     h = T + V
     nocc = mol.n_atoms
     ctx = df.Context(mol.nao, mol.naux, nocc)
-    ctx.setup(inputs.df_tensor_device(mol))
+    if mol.n_atoms >= 120:
+        # the library forms B from the integrals on the device (Cholesky + triangular solve)
+        Tg = torch.from_numpy(inputs.int3c(mol)).cuda()
+        Vg = torch.from_numpy(inputs.metric(mol)).cuda()
+        Bg = ctx.setup_integrals(Tg, Vg)
+        del Vg
+    else:
+        Bg = inputs.df_tensor_device(mol)
+        ctx.setup(Bg)
     runs = {}
     for name, kw in (("fp64", {"mode": "fp64"}), ("rule", {"mode": "rule"}),
                      ("rule_level0_8_slices", {"mode": "rule", "level0_slices": 8}),

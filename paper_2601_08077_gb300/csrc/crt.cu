@@ -151,6 +151,22 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
   return v;
 }
 
+// Largest absolute bit pattern over the TPR threads of a row (a warp, or the
+// whole 256-thread block through shared memory).
+template <int TPR>
+__device__ __forceinline__ uint64_t row_max_u64(uint64_t m) {
+  m = warp_max_u64(m);
+  if (TPR > 32) {
+    __shared__ uint64_t part[TPR / 32];
+    const int w = (threadIdx.x & (TPR - 1)) >> 5;
+    if ((threadIdx.x & 31) == 0) part[w] = m;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TPR / 32; ++i) m = part[i] > m ? part[i] : m;
+  }
+  return m;
+}
+
 // RNE(v 2^(q1 - e)) as int64 for |v| < 127/128 2^e and q1 <= 62.  Integer-only.
 __device__ __forceinline__ long long scaled_rne_q(uint64_t bits, int e, int q1) {
   int E = (int)((bits >> 52) & 0x7FF);
@@ -195,27 +211,28 @@ __device__ __forceinline__ int residue(int lo, int hi, const CrtTab &t, int i) {
   return r > (m >> 1) ? r - m : r;
 }
 
-// One warp per row: exponent, scaled integers, residue planes.  kInspect
-// writes the residues as int16 (inspection entry point), else BF16 bits.
-template <bool kInspect>
+// TPR threads per row (a warp, or the whole block for wide rows): exponent,
+// scaled integers, residue planes.  kInspect writes the residues as int16
+// (inspection entry point), else BF16 bits.
+template <bool kInspect, int TPR>
 __global__ void __launch_bounds__(256)
     crt_split_rows_kernel(const double *__restrict__ A, long long rows, int cols, long long ld, const CrtTab t,
                           int *__restrict__ exps, uint16_t *__restrict__ planes, long long dld, long long pstride) {
-  const int lane = threadIdx.x & 31;
-  const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= rows) return;
+  const int lane = threadIdx.x & (TPR - 1);
+  const long long r = (long long)blockIdx.x * (blockDim.x / TPR) + (threadIdx.x / TPR);
+  if (r >= rows) return;  // uniform over a row's threads
   const double *row = A + r * ld;
   uint64_t mx = 0;
-  for (int c = lane; c < cols; c += 32) {
+  for (int c = lane; c < cols; c += TPR) {
     const uint64_t a = abs_bits(__ldg(row + c));
     mx = a > mx ? a : mx;
   }
-  mx = warp_max_u64(mx);
+  mx = row_max_u64<TPR>(mx);
   const int e = exponent_from_max_bits_dev(mx);
   if (lane == 0) exps[r] = e;
   uint16_t *drow = planes + r * dld;
   // four columns per lane per step: four independent chains per residue
-  for (int c = 4 * lane; c < cols; c += 128) {
+  for (int c = 4 * lane; c < cols; c += 4 * TPR) {
     const int nv = cols - c < 4 ? cols - c : 4;
     int lo[4], hi[4];
 #pragma unroll
@@ -295,11 +312,19 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_crt_split(const double *A, long long rows, int cols, long long ld, const CrtTab &t, int *exps,
                              uint16_t *planes, long long dld, long long pstride, bool inspect, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((rows + 7) / 8));
-  if (inspect)
-    crt_split_rows_kernel<true><<<grid, 256, 0, st>>>(A, rows, cols, ld, t, exps, planes, dld, pstride);
-  else
-    crt_split_rows_kernel<false><<<grid, 256, 0, st>>>(A, rows, cols, ld, t, exps, planes, dld, pstride);
+  if (cols >= kWideRow) {
+    const dim3 grid((unsigned)rows);
+    if (inspect)
+      crt_split_rows_kernel<true, 256><<<grid, 256, 0, st>>>(A, rows, cols, ld, t, exps, planes, dld, pstride);
+    else
+      crt_split_rows_kernel<false, 256><<<grid, 256, 0, st>>>(A, rows, cols, ld, t, exps, planes, dld, pstride);
+  } else {
+    const dim3 grid((unsigned)((rows + 7) / 8));
+    if (inspect)
+      crt_split_rows_kernel<true, 32><<<grid, 256, 0, st>>>(A, rows, cols, ld, t, exps, planes, dld, pstride);
+    else
+      crt_split_rows_kernel<false, 32><<<grid, 256, 0, st>>>(A, rows, cols, ld, t, exps, planes, dld, pstride);
+  }
   return cudaGetLastError();
 }
 
@@ -315,24 +340,28 @@ df_status crt_gemm(const double *A, const double *B, int M, int N, int K, int nm
   if (!make_tab(K, nmod, &t)) return DF_ERR_ARG;
   const long long ld = round_up_ll(K, 8);
   const long long ldy = round_up_ll(N, 16);
+  // A B^T with B == A (a Gram matrix such as K_b = X_b X_b^T): one split serves both sides
+  const bool same = A == B && M == N;
   uint16_t *Ad = nullptr, *Bd = nullptr;
   uint8_t *Y = nullptr;
   int *ea = nullptr, *eb = nullptr, *status = nullptr;
   df_status rs = DF_OK;
   cudaError_t e = scratch_malloc((void **)&Ad, sizeof(uint16_t) * (size_t)nmod * M * ld, st);
-  if (e == cudaSuccess) e = scratch_malloc((void **)&Bd, sizeof(uint16_t) * (size_t)nmod * N * ld, st);
+  if (e == cudaSuccess && !same) e = scratch_malloc((void **)&Bd, sizeof(uint16_t) * (size_t)nmod * N * ld, st);
   if (e == cudaSuccess) e = scratch_malloc((void **)&Y, (size_t)nmod * M * ldy, st);
   if (e == cudaSuccess) e = scratch_malloc((void **)&ea, sizeof(int) * M, st);
-  if (e == cudaSuccess) e = scratch_malloc((void **)&eb, sizeof(int) * N, st);
+  if (e == cudaSuccess && !same) e = scratch_malloc((void **)&eb, sizeof(int) * N, st);
   if (e == cudaSuccess) e = scratch_malloc((void **)&status, sizeof(int), st);
   if (e == cudaErrorMemoryAllocation) rs = DF_ERR_OOM;
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e == cudaSuccess) e = launch_crt_split(A, M, K, K, t, ea, Ad, ld, (long long)M * ld, false, st);
-  if (e == cudaSuccess) e = launch_crt_split(B, N, K, K, t, eb, Bd, ld, (long long)N * ld, false, st);
+  if (e == cudaSuccess && !same) e = launch_crt_split(B, N, K, K, t, eb, Bd, ld, (long long)N * ld, false, st);
+  const uint16_t *Bplanes = same ? Ad : Bd;
+  const int *ebx = same ? ea : eb;
   if (e == cudaSuccess) {
     CUtensorMap ta, tb;
     if (!make_tmap_bf16(&ta, Ad, K, M, nmod, ld, (long long)M * ld) ||
-        !make_tmap_bf16(&tb, Bd, K, N, nmod, ld, (long long)N * ld)) {
+        !make_tmap_bf16(&tb, Bplanes, K, N, nmod, ld, (long long)N * ld)) {
       rs = DF_ERR_CUDA;
     } else {
       SgParams p;
@@ -358,7 +387,7 @@ df_status crt_gemm(const double *A, const double *B, int M, int N, int K, int nm
   }
   if (e == cudaSuccess && rs == DF_OK && out) {
     const dim3 grid((unsigned)((N + 255) / 256), (unsigned)(M < 65535 ? M : 65535));
-    crt_reconstruct_kernel<<<grid, 256, 0, st>>>(Y, M, N, ldy, (long long)M * ldy, ea, eb, t, out, N);
+    crt_reconstruct_kernel<<<grid, 256, 0, st>>>(Y, M, N, ldy, (long long)M * ldy, ea, ebx, t, out, N);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && rs == DF_OK && Y_user)
@@ -366,7 +395,7 @@ df_status crt_gemm(const double *A, const double *B, int M, int N, int K, int nm
   if (e == cudaSuccess && rs == DF_OK && ea_user)
     e = cudaMemcpyAsync(ea_user, ea, sizeof(int) * M, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && rs == DF_OK && eb_user)
-    e = cudaMemcpyAsync(eb_user, eb, sizeof(int) * N, cudaMemcpyDeviceToDevice, st);
+    e = cudaMemcpyAsync(eb_user, ebx, sizeof(int) * N, cudaMemcpyDeviceToDevice, st);
   int h = 0;
   if (e == cudaSuccess && rs == DF_OK) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   for (void *ptr : {(void *)Ad, (void *)Bd, (void *)Y, (void *)ea, (void *)eb, (void *)status})

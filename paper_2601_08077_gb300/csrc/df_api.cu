@@ -610,19 +610,25 @@ df_status grid_gemm(const double *A, const double *B, int M, int N, int K, int s
                     double *out, int32_t *ea_out, int32_t *eb_out, cudaStream_t st) {
   if (!A || !B || M <= 0 || N <= 0 || K <= 0 || s < 1 || s > DF_S_MAX) return DF_ERR_ARG;
   const long long ld = round_up(K, 8);
+  // A B^T with B == A (a Gram matrix such as K_b = X_b X_b^T): one split serves both sides
+  const bool same = A == B && M == N;
   uint16_t *Ad = nullptr, *Bd = nullptr;
   int *ea = nullptr, *eb = nullptr, *status = nullptr;
   df_status rs = DF_OK;
   cudaError_t e = df::scratch_malloc((void **)&Ad, sizeof(uint16_t) * (size_t)s * M * ld, st);
-  if (e == cudaSuccess) e = df::scratch_malloc((void **)&Bd, sizeof(uint16_t) * (size_t)s * N * ld, st);
+  if (e == cudaSuccess && !same) e = df::scratch_malloc((void **)&Bd, sizeof(uint16_t) * (size_t)s * N * ld, st);
   if (e == cudaSuccess) e = df::scratch_malloc((void **)&ea, sizeof(int) * M, st);
-  if (e == cudaSuccess) e = df::scratch_malloc((void **)&eb, sizeof(int) * N, st);
+  if (e == cudaSuccess && !same) e = df::scratch_malloc((void **)&eb, sizeof(int) * N, st);
   if (e == cudaSuccess) e = df::scratch_malloc((void **)&status, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
   // raw mode adds every chunk into its group's output: start from zero
   if (e == cudaSuccess && mode == df::kModeRaw) e = cudaMemsetAsync(raw, 0, sizeof(int64_t) * (size_t)s * M * N, st);
   if (e == cudaSuccess) e = df::launch_split_rows_bf16(A, M, K, K, s, ea, Ad, ld, (long long)M * ld, st);
-  if (e == cudaSuccess) e = df::launch_split_rows_bf16(B, N, K, K, s, eb, Bd, ld, (long long)N * ld, st);
+  if (e == cudaSuccess && !same) e = df::launch_split_rows_bf16(B, N, K, K, s, eb, Bd, ld, (long long)N * ld, st);
+  if (same) {
+    Bd = Ad;
+    eb = ea;
+  }
   if (e == cudaSuccess) {
     CUtensorMap ta, tb;
     if (!df::make_tmap_bf16(&ta, Ad, K, M, s, ld, (long long)M * ld) ||
@@ -654,7 +660,7 @@ df_status grid_gemm(const double *A, const double *B, int M, int N, int K, int s
   if (e == cudaSuccess && rs == DF_OK) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && rs == DF_OK && ea_out) e = cudaMemcpyAsync(ea_out, ea, sizeof(int) * M, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && rs == DF_OK && eb_out) e = cudaMemcpyAsync(eb_out, eb, sizeof(int) * N, cudaMemcpyDeviceToDevice, st);
-  for (void *ptr : {(void *)Ad, (void *)Bd, (void *)ea, (void *)eb, (void *)status})
+  for (void *ptr : {(void *)Ad, same ? nullptr : (void *)Bd, (void *)ea, same ? nullptr : (void *)eb, (void *)status})
     if (ptr) cudaFreeAsync(ptr, st);
   cudaError_t es = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = es;

@@ -40,6 +40,10 @@ enum SgLayout : int {
 
 constexpr int kCrtMaxModuli = 16;
 
+// Row splits give a whole 256-thread block to each row at least this wide
+// (fewer, longer rows: the second exchange GEMM's operands), else a warp.
+constexpr int kWideRow = 2048;
+
 struct SgParams {
   int layout, mode;
   int nunits;

@@ -31,16 +31,35 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
   return v;
 }
 
-// One warp per row; two columns per lane per step (16-byte loads, 4-byte stores).
+// Largest absolute bit pattern over the TPR threads of a row (TPR = 32: one
+// warp; TPR = 256: the whole block, through shared memory).
+template <int TPR>
+__device__ __forceinline__ uint64_t row_max_u64(uint64_t m) {
+  m = warp_max_u64(m);
+  if (TPR > 32) {
+    __shared__ uint64_t part[TPR / 32];
+    const int w = (threadIdx.x & (TPR - 1)) >> 5;
+    if ((threadIdx.x & 31) == 0) part[w] = m;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TPR / 32; ++i) m = part[i] > m ? part[i] : m;
+  }
+  return m;
+}
+
+// TPR threads per row (a warp, or the whole block for wide rows so that a
+// few hundred rows of tens of thousands of columns still fill the GPU); two
+// columns per thread per step (16-byte loads, 4-byte stores).
+template <int TPR>
 __global__ void __launch_bounds__(256) split_rows_bf16_kernel(const double *__restrict__ A, long long rows,
                                                               int cols, long long ld, int nslices,
                                                               int *__restrict__ exps,
                                                               uint16_t *__restrict__ digits, long long dld,
                                                               long long plane_stride, int vec2,
                                                               const int *__restrict__ perm, int group) {
-  const int lane = threadIdx.x & 31;
-  const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= rows) return;
+  const int lane = threadIdx.x & (TPR - 1);
+  const long long r = (long long)blockIdx.x * (blockDim.x / TPR) + (threadIdx.x / TPR);
+  if (r >= rows) return;  // uniform over a row's threads (a whole block when TPR = 256)
   // with a permutation, output row r = (P', j) reads input row (perm[P'], j), `group` rows per P
   const long long src = perm ? (long long)perm[r / group] * group + (r % group) : r;
   const double *row = A + src * ld;
@@ -48,7 +67,7 @@ __global__ void __launch_bounds__(256) split_rows_bf16_kernel(const double *__re
   if (vec2) {
     const double2 *row2 = reinterpret_cast<const double2 *>(row);
     const int half = cols >> 1;
-    for (int c = lane; c < half; c += 32) {
+    for (int c = lane; c < half; c += TPR) {
       double2 v = __ldg(row2 + c);
       uint64_t a = abs_bits(v.x), b = abs_bits(v.y);
       m = a > m ? a : m;
@@ -59,16 +78,16 @@ __global__ void __launch_bounds__(256) split_rows_bf16_kernel(const double *__re
       m = a > m ? a : m;
     }
   } else {
-    for (int c = lane; c < cols; c += 32) {
+    for (int c = lane; c < cols; c += TPR) {
       uint64_t a = abs_bits(__ldg(row + c));
       m = a > m ? a : m;
     }
   }
-  m = warp_max_u64(m);
+  m = row_max_u64<TPR>(m);
   const int e = exponent_from_max_bits_dev(m);
   if (lane == 0) exps[r] = e;
   uint16_t *drow = digits + r * dld;
-  for (int c = 2 * lane; c < cols; c += 64) {
+  for (int c = 2 * lane; c < cols; c += 2 * TPR) {
     int d0[kSMax], d1[kSMax];
     uint64_t b0 = (uint64_t)__double_as_longlong(row[c]);
     balanced_digits(scaled_rne(b0, e), d0);
@@ -370,10 +389,16 @@ cudaError_t launch_split_rows_bf16(const double *A, long long rows, int cols, lo
                                    cudaStream_t st, const int *perm, int group) {
   if (rows <= 0) return cudaSuccess;
   const int vec2 = ((ld & 1) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) ? 1 : 0;
-  const int wpb = 8;
-  dim3 grid((unsigned)((rows + wpb - 1) / wpb));
-  split_rows_bf16_kernel<<<grid, 32 * wpb, 0, st>>>(A, rows, cols, ld, nslices, exps, digits, dld,
-                                                    plane_stride, vec2, perm, group > 0 ? group : 1);
+  const int g = group > 0 ? group : 1;
+  if (cols >= kWideRow) {
+    split_rows_bf16_kernel<256><<<(unsigned)rows, 256, 0, st>>>(A, rows, cols, ld, nslices, exps, digits, dld,
+                                                                 plane_stride, vec2, perm, g);
+  } else {
+    const int wpb = 8;
+    dim3 grid((unsigned)((rows + wpb - 1) / wpb));
+    split_rows_bf16_kernel<32><<<grid, 32 * wpb, 0, st>>>(A, rows, cols, ld, nslices, exps, digits, dld,
+                                                         plane_stride, vec2, perm, g);
+  }
   return cudaGetLastError();
 }
 

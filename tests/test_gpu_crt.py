@@ -98,3 +98,27 @@ def test_rejects_bad_arguments(df):
     assert e.value.status == -1
     with pytest.raises(df.DFError):
         df.emulated_gemm_crt(A, A, 1)
+
+
+@pytest.mark.parametrize("nmod", [8, 13])
+def test_gram_product_shares_one_split(df, nmod):
+    # A B^T with B the same tensor as A (K_b = X_b X_b^T): one split on the device,
+    # rows wider than 2048 (a whole block per row)
+    rng = np.random.default_rng(40 + nmod)
+    A = _mat(rng, 150, 2500, spread=5.0, zero_row=4)
+    At = torch.from_numpy(A).cuda()
+    out = df.emulated_gemm_crt(At, At, nmod).cpu().numpy()
+    assert np.array_equal(out, CO.emulated_gemm_crt(A, A, nmod))
+    assert np.array_equal(out, out.T)
+
+
+@pytest.mark.parametrize("s", [3, 5])
+def test_slice_gram_product_shares_one_split(df, s):
+    from oracle import df_oracle as O
+    rng = np.random.default_rng(60 + s)
+    A = _mat(rng, 140, 2500, spread=5.0, zero_row=7)
+    At = torch.from_numpy(A).cuda()
+    out = df.emulated_gemm(At, At, s).cpu().numpy()
+    assert np.array_equal(out, O.emulated_matmul(A, A.T, s))      # T = 0 here: bit-exact
+    Bt = At.clone()                                                 # a different pointer: two splits
+    assert np.array_equal(df.emulated_gemm(At, Bt, s).cpu().numpy(), out)
