@@ -219,6 +219,15 @@ df_status df_adaptive_next(df_ctx *ctx, double energy, int *level_out, int *nsli
 
 /* Read (and clear) the device status word; synchronises `stream`. */
 df_status df_sync_status(df_ctx *ctx, void *stream);
+
+/* Failure-path self-test, without a GPU fault: one thread waits, through the
+ * same bounded-wait routine the slice-GEMM pipeline uses, on a barrier that
+ * nothing completes; after limit_ms (1 to 10000) the wait gives up, sets the
+ * abort flag and the status word, and the kernel returns.  Returns
+ * DF_ERR_TIMEOUT when the wait ran out and was reported (the expected
+ * result), DF_OK if it was not, DF_ERR_CUDA on a CUDA error.  The CUDA
+ * context stays usable.  Synchronises `stream`. */
+df_status df_selftest_wait_timeout(int limit_ms, void *stream);
 df_status df_last_error(const df_ctx *ctx);
 const char *df_strerror(df_status s);
 

@@ -579,6 +579,21 @@ df_status df_adaptive_next(df_ctx *c, double energy, int *level_out, int *nslice
   return DF_OK;
 }
 
+df_status df_selftest_wait_timeout(int limit_ms, void *stream) {
+  if (limit_ms < 1 || limit_ms > 10000) return DF_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  int *status = nullptr;
+  int h = 0;
+  cudaError_t e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = df::launch_wait_selftest(status, (unsigned long long)limit_ms * 1000000ull, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (status) cudaFree(status);
+  if (e != cudaSuccess) return DF_ERR_CUDA;
+  return h == 1 ? DF_ERR_TIMEOUT : DF_OK;
+}
+
 df_status df_sync_status(df_ctx *c, void *stream) {
   if (!c) return DF_ERR_ARG;
   cudaStream_t st = as_stream(stream);

@@ -139,6 +139,10 @@ cudaError_t launch_slice_gemm(const SgParams &p, const CUtensorMap &ta, const CU
 cudaError_t launch_slice_gemm_grouped(int mode, const SgGroup &g, int *status, int grid, cudaStream_t st,
                                       bool pairs = false);
 int slice_gemm_grid(int nunits);
+// One-thread kernel whose bounded wait on a never-completed mbarrier runs out
+// after limit_ns and sets bit 0 of *status (bit 1: it returned without the
+// abort path, which would be a defect).
+cudaError_t launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t st);
 int fixed_point_shift(int s, long long k);
 
 cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st);

@@ -144,14 +144,15 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t pa
 // Bounded wait.  Returns false if the CTA is aborting or the wait ran out.
 template <bool kCluster = false>
 __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                             int *status, bool honour_abort = true) {
+                                             int *status, bool honour_abort = true,
+                                             uint64_t limit_ns = kTimeoutNs) {
   auto poll = [&]() { return kCluster ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
   if (poll()) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
     if (poll()) return true;
     if (honour_abort && *abort_flag) return false;
-    if (globaltimer_ns() - t0 > kTimeoutNs) {
+    if (globaltimer_ns() - t0 > limit_ns) {
       *abort_flag = 1;
       atomicOr(status, 1);
       return false;
@@ -834,6 +835,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Failure-path self-test of the bounded wait: one thread waits, through the
+// pipeline's own wait routine, on an mbarrier that expects an arrival nobody
+// makes.  The wait gives up after limit_ns, raises the CTA's abort flag and
+// the status bit, and the kernel returns normally (no trap, no fault).
+__global__ void wait_selftest_kernel(int *status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!wait_bounded<false>(&bar, 0, &abort_flag, status, true, limit_ns) && !abort_flag) atomicOr(status, 2);
+  }
+}
+
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                     const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                                     CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -880,6 +898,11 @@ int fixed_point_shift(int s, long long k) {
   int bits = 0;
   while (ldexpl(1.0L, bits) < bound) ++bits;
   return bits > 61 ? bits - 61 : 0;
+}
+
+cudaError_t launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(status, limit_ns);
+  return cudaGetLastError();
 }
 
 int slice_gemm_grid(int nunits) {

@@ -69,6 +69,7 @@ def lib():
         L.df_adaptive_level0.argtypes = [P, I]
         L.df_adaptive_next.argtypes = [P, D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.df_sync_status.argtypes = [P, V]
+        L.df_selftest_wait_timeout.argtypes = [I, V]
         L.df_last_error.argtypes = [P]
         L.df_strerror.argtypes = [I]
         L.df_strerror.restype = ctypes.c_char_p
@@ -173,6 +174,11 @@ def emulated_gemm(A: torch.Tensor, B: torch.Tensor, nslices: int, stream=None):
     _check(lib().df_emulated_gemm(_f64(A), _f64(B), M, N, K, nslices, _ptr(out), _stream(stream)),
            "df_emulated_gemm")
     return out
+
+
+def selftest_wait_timeout(limit_ms: int = 1000, stream=None) -> int:
+    """Run the bounded-wait failure self-test; returns its status (DF_ERR_TIMEOUT = -5 expected)."""
+    return lib().df_selftest_wait_timeout(int(limit_ms), _stream(stream))
 
 
 def crt_modulus(i: int) -> int:

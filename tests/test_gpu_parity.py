@@ -422,3 +422,19 @@ def test_setup_from_integrals_rejects_indefinite_metric(df):
         ctx.setup_integrals(Tg, cuda(V))
     assert e.value.status == -4  # DF_ERR_NOT_PD
     assert np.array_equal(Tg.cpu().numpy(), T)
+
+
+def test_bounded_wait_reports_a_timeout_and_the_context_survives(df, small):
+    """Failure detection without a fault: a wait on a barrier nothing completes
+    runs out after its limit, is reported as DF_ERR_TIMEOUT, and the next
+    build on the same context is still correct."""
+    import time
+    t0 = time.perf_counter()
+    assert df.selftest_wait_timeout(300) == -5
+    dt = time.perf_counter() - t0
+    assert 0.29 <= dt < 30.0
+    B, C, D = small
+    ctx, _ = _ctx(df, B, C.shape[1])
+    K, _ = ctx.build_K(cuda(C), 0)
+    ctx.sync_status()
+    assert np.allclose(K.cpu().numpy(), O.exchange(B, C), rtol=0, atol=1e-12 * np.abs(O.exchange(B, C)).max())
