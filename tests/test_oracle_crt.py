@@ -111,3 +111,14 @@ def test_agrees_with_slices_at_matching_width():
         e_crt = np.max(np.abs(CO.emulated_gemm_crt(A, B, n) - ref))
         e_sl = np.max(np.abs(O.emulated_matmul(A, B.T, s) - ref))
         assert e_crt <= 4 * e_sl
+
+
+def test_transpose_and_power_of_two_scaling_are_exact():
+    # the procedure treats rows of A and rows of B alike, and a power-of-two
+    # scale only moves the row exponent
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((5, 30)) * np.exp(rng.uniform(-3, 3, (5, 1)))
+    B = rng.standard_normal((4, 30))
+    out = CO.emulated_gemm_crt(A, B, 9)
+    assert np.array_equal(CO.emulated_gemm_crt(B, A, 9), out.T)
+    assert np.array_equal(CO.emulated_gemm_crt(A * 2.0 ** 37, B * 2.0 ** -11, 9), out * 2.0 ** 26)

@@ -79,3 +79,22 @@ def test_scf_converges_and_is_stationary():
     assert np.allclose(Dm @ S @ Dm, 2.0 * Dm, atol=1e-10)          # idempotent (D S D = 2 D)
     assert abs(np.sum(Dm * S) - 2 * mol.n_atoms) < 1e-9            # electron count
     assert res["E"] < res["history"][0]
+
+
+def test_scf_energy_is_invariant_to_the_order_of_atoms_and_aux_functions():
+    # relabelling basis functions (atom order) and auxiliary functions changes
+    # every matrix but not the physics: a dropped term or a transposed index
+    # in the Fock build would break this
+    mol, B, C, D = inputs.make_inputs(inputs.SMALL)
+    Z = inputs.nuclear_charges(mol)
+    S = SO.overlap(mol.ao_xyz, mol.ao_exp)
+    h = SO.kinetic(mol.ao_xyz, mol.ao_exp) + SO.nuclear(mol.ao_xyz, mol.ao_exp, mol.xyz, Z)
+    En = SO.nuclear_repulsion(mol.xyz, Z)
+    ref = SO.scf(h, S, mol.n_atoms, SO.df_jk(B), En)
+    rng = np.random.default_rng(5)
+    p = rng.permutation(mol.nao)
+    q = rng.permutation(B.shape[0])
+    Bp = np.ascontiguousarray(B[q][:, p][:, :, p])
+    res = SO.scf(h[np.ix_(p, p)], S[np.ix_(p, p)], mol.n_atoms, SO.df_jk(Bp), En)
+    assert res["converged"] and ref["converged"]
+    assert abs(res["E"] - ref["E"]) < 1e-9
