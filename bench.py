@@ -3,10 +3,10 @@
 
 One step = one SCF-like iteration of the paper's method on one synthetic
 molecule: the FP64 Coulomb build (rho, J), the exchange build with both
-contractions emulated over INT8 slices, the energies, and the adaptive
-precision rule (Table 1) picking the next slice count.  The slice count in the
-timed steps is the one the rule selects at level 2 (5 slices), the first level
-whose emulation meets max|dK| <= 1e-10 max|K|; every run checks that gate
+contractions emulated over INT8 slices, and the energies.  Every timed step
+runs a fixed slice count, by default 5, Table 1's level-2 count and the first
+level whose emulation meets max|dK| <= 1e-10 max|K|; every run checks that
+gate against the CPU oracle's K, J and energies (all auxiliary blocks) and
 against the native-FP64 build of the same K on the same GPU.
 
 metric: effective FP64 TFLOP/s of the exchange build, F_K = 4 nao^2 naux nocc
@@ -136,26 +136,49 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(B, C, w, budget_s=15.0):
-    """The oracle as it stands on the host cores, on a bounded sample: the exchange
-    build of whole 128-function auxiliary blocks, scaled to the metric's unit.
-    B may live on the device; each sampled block is copied to the host first."""
+def oracle_reference(B, C, D, w):
+    """The oracle as it stands, on the host cores, over every 128-function
+    auxiliary block of the workload: the exchange build of the block's B_P
+    (Eqs. df-k-1/2), its rho_P (Eq. df-j-1) and its share of J (Eq. df-j-2).
+    K and J are the FP64 sums over blocks, the accuracy reference of the run.
+    The exchange part is timed for cpu_baseline (about 8 s for the 240-atom
+    molecule on 16 cores).  B may live on the device; each block is copied to
+    the host first (not timed)."""
     from oracle import df_oracle as O
     cores = len(os.sched_getaffinity(0))
-    nb, t_total, flops = 0, 0.0, 0.0
-    while t_total < budget_s and nb * 128 < w.naux:
-        p0, p1 = nb * 128, min(w.naux, nb * 128 + 128)
+    nblk = (w.naux + 127) // 128
+    K = np.zeros((w.nao, w.nao))
+    J = np.zeros((w.nao, w.nao))
+    rho = np.empty(w.naux)
+    t_total, flops = 0.0, 0.0
+    for b in range(nblk):
+        p0, p1 = b * 128, min(w.naux, b * 128 + 128)
         Bb = B[p0:p1]
         Bb = Bb.cpu().numpy() if hasattr(Bb, "cpu") else Bb
         t0 = time.perf_counter()
-        O.exchange(Bb, C)
+        Kb = O.exchange(Bb, C)
         t_total += time.perf_counter() - t0
         flops += 4.0 * w.nao ** 2 * (p1 - p0) * w.nocc
-        nb += 1
-    return {"value": flops / t_total / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "oracle FP64 exchange build (NumPy, Eqs. df-k-1/2) of %d of %d auxiliary blocks "
-                      "(%d functions) of the %s workload, %.1f s" % (nb, (w.naux + 127) // 128,
-                                                                     min(w.naux, nb * 128), w.name, t_total)}
+        K += Kb
+        rho[p0:p1] = O.rho(Bb, D)
+        J += O.coulomb(Bb, rho[p0:p1])
+    base = {"value": flops / t_total / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle FP64 exchange build (NumPy, Eqs. df-k-1/2) of all %d auxiliary blocks "
+                      "(%d functions) of the %s workload, %.1f s" % (nblk, w.naux, w.name, t_total)}
+    return base, K, J, rho
+
+
+def oracle_gate(K_gpu, J_gpu, E_gpu, K_ref, J_ref, D):
+    """Errors of the run's K (at the timed slice count), J and E_J + E_K against the
+    oracle's, and the gate of the metric: max|dK| <= 1e-10 max|K| and |dE| <= 1e-9 Eh."""
+    from oracle import df_oracle as O
+    EJ, EK = O.energies(D, J_ref, K_ref)
+    dK = float(np.max(np.abs(K_gpu - K_ref)) / np.max(np.abs(K_ref)))
+    dJ = float(np.max(np.abs(J_gpu - J_ref)) / np.max(np.abs(J_ref)))
+    dE = abs((E_gpu[0] + E_gpu[2]) - (EJ + EK))
+    return {"max_dK_rel_vs_oracle": dK, "max_dJ_rel_vs_oracle": dJ, "dE_vs_oracle": dE,
+            "dEJ_vs_oracle": abs(E_gpu[0] - EJ), "dEK_vs_oracle": abs(E_gpu[2] - EK),
+            "E_oracle": EJ + EK, "gate_vs_oracle": bool(dK <= 1e-10 and dE <= 1e-9)}
 
 
 def run_reference(args, w):
@@ -516,14 +539,13 @@ def main():
     E_s = ctx.energy(Dg, J, Ks, rho)
     dE = abs((E_s[0] + E_s[2]) - (E_fp64[0] + E_fp64[2]))
     ctx.sync_status()
-
-    ctx.adaptive_reset()
+    K_gate, J_gate = Ks.cpu().numpy(), J.cpu().numpy()
+    del Ks, K64
 
     def step():
         ctx.build_J(Dg, J, rho)
         ctx.build_K(Cg, s, K)
-        e = ctx.energy(Dg, J, K, rho)
-        ctx.adaptive_next(e[0] + e[2])
+        ctx.energy(Dg, J, K, rho)
 
     for _ in range(args.warmup):
         step()
@@ -571,11 +593,10 @@ def main():
         Dd.copy_(Dh, non_blocking=True)
         ctx.build_J(Dd, J, rho)
         ctx.build_K(Cd, s, K)
-        e = ctx.energy(Dd, J, K, rho)
+        ctx.energy(Dd, J, K, rho)
         Jh.copy_(J, non_blocking=True)
         Kh.copy_(K, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-        ctx.adaptive_next(e[0] + e[2])
 
     step_e2e()
     torch.cuda.synchronize()
@@ -608,7 +629,8 @@ def main():
         "vs_baseline": None, "dtype": "f64 (INT8 slices as BF16 on tcgen05, exact INT accumulation)",
         "data": "synthetic (seeded s-type Gaussian molecule, integrals and DF tensor generated)",
         "config": {"workload": w.name, "nao": w.nao, "naux": w.naux, "nocc": w.nocc, "nslices": s,
-                   "level": 2, "l2": "inputs larger than L2 (B %.1f GB)" % (B_bytes / 1e9),
+                   "slice_count": "fixed for every step (5 = Table 1 level 2's count, the first level meeting "
+                                  "max|dK| <= 1e-10 max|K|)" if s == 5 else "fixed for every step", "l2": "inputs larger than L2 (B %.1f GB)" % (B_bytes / 1e9),
                    "cluster_pairs": args.cluster_pairs,
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": FK / (ms_e2e * 1e-3) / 1e12 * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -627,7 +649,10 @@ def main():
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(Bg, C, w)
+        out["cpu_baseline"], K_ref, J_ref, _ = oracle_reference(Bg, C, D, w)
+        out["accuracy"].update(oracle_gate(K_gate, J_gate, E_s, K_ref, J_ref, D))
+        if not out["accuracy"]["gate_vs_oracle"]:
+            print("bench: the run misses the accuracy gate against the oracle", file=sys.stderr)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

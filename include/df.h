@@ -147,11 +147,16 @@ df_status df_emulated_gemm(const double *A_dev, const double *B_dev, int M, int 
  * as a framework whose memory pool already holds nearly all device memory, or
  * a latency-critical loop that cannot take the synchronisation of
  * cudaMalloc/cudaFree).  Scratch comes from one static 32 MiB device array per
- * GPU; sizes needing more than that (digit planes 2 * nslices * (M + N) *
- * round_up(K, 8) bytes plus exponents) return DF_ERR_SCRATCH.  The first call
- * on a device looks up the array's device address with that device current:
- * make it before any stream capture.  Calls share the array, so calls whose
- * GPU work overlaps race.  Synchronises `stream`. */
+ * GPU; sizes needing more than that return DF_ERR_SCRATCH.  The scratch
+ * needed is, with every part rounded up to 256 bytes: a 4-byte status word,
+ * 4 M + 4 N bytes of exponents and 2 * nslices * (M + N) * round_up(K, 8)
+ * bytes of digit planes; when B_dev == A_dev and N == M (a Gram product) one
+ * split serves both operands and the N terms drop out.  The first call on a
+ * device looks up the array's device address with that device current: make
+ * it before any stream capture.  The address is kept for the process's life,
+ * so after a cudaDeviceReset this entry point must not be called on that
+ * device again.  Calls share the array, so calls whose GPU work overlaps
+ * race.  Synchronises `stream`. */
 df_status df_emulated_gemm_static(const double *A_dev, const double *B_dev, int M, int N, int K, int nslices,
                                   double *out_dev, void *stream);
 

@@ -7,6 +7,14 @@ K error meets the block's share of the tolerance) and of the block features.
 The predictor is not in the paper; it extends the paper's closing suggestion
 (Section 5) of tying the emulation level to the change of the density matrix,
 with the per-block error budget read as an additive split of the tolerance.
+Training uses Adam (Kingma and Ba, 2015: moments with decay 0.9 / 0.999, bias
+correction by 1 - beta^t, eps 1e-8), restated in ``adam_step``.
+
+Pins (tests/test_oracle_mlp.py): backpropagation against finite
+differences; the forward pass of a hand-set network whose logits are worked
+out by hand (a missing ReLU or a transposed weight fails it); Adam's closed
+forms (first step lr sign(g), constant gradient, zero gradient); the block
+features of a hand-built tensor whose 16 values are worked out by hand.
 
 Parameter layout (as in the CUDA library): W1[64][16], b1[64], W2[64][64],
 b2[64], W3[8][64], b3[8].
@@ -79,6 +87,20 @@ def gradients(theta, X, y):
     return pack(g)
 
 
+def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update at step t (1-based); returns (theta', m', v').
+
+    m' = beta1 m + (1 - beta1) g, v' = beta2 v + (1 - beta2) g^2,
+    theta' = theta - lr (m' / (1 - beta1^t)) / (sqrt(v' / (1 - beta2^t)) + eps).
+    """
+    g = np.asarray(grad, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return np.asarray(theta, dtype=np.float64) - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
 def labels(err, kmax, tau, nblk):
     """Least s (1..8) with max|K_b(s) - K_b(FP64)| <= tau max|K| / nblk; 8 if none."""
     budget = tau * kmax / nblk
@@ -91,24 +113,53 @@ def labels(err, kmax, tau, nblk):
 
 
 def block_features(B, eB, nocc, tau, dD, dE, s_rule, block=128):
-    """The 16 features of every block (same definitions and scalings as the library)."""
+    """The 16 input features of every auxiliary block b (rows P in the block).
+
+    With Bb the block's slice of B, eB the per-(P, mu) row exponents of the
+    split (a zero row counts with exponent 0), rows = all (P, mu) rows of the
+    block, Emax / Emin their largest / smallest exponent, ss_b = sum Bb^2 and
+    max_b = max|Bb|:
+
+      0  log2(max_b) / 32                  8  log2(nao) / 12
+      1  log2(sqrt(ss_b)) / 32             9  log2(nocc) / 10
+      2  mean of eB over rows / 32         10 log2(ss_b / sum_b' ss_b') / 32
+      3  (Emax - Emin) / 32                11 fraction of rows with eB < Emax - 20
+      4  log10(tau) / 16                   12 s_rule / 8
+      5  log10(dD + 1e-30) / 16            13 (log2(max_b) - log2(max_b' max_b')) / 32
+      6  b / nblk                          14 log10(dE + 1e-30) / 16
+      7  log2(number of P in the block) / 8  15 1 (bias input)
+
+    A tiny 1e-300 is added inside every log2 of a norm, so an all-zero block
+    gives finite features.
+    """
     naux, nao, _ = B.shape
     nblk = (naux + block - 1) // block
-    st = []
+    tiny = 1e-300
+    maxes, sums = [], []
     for b in range(nblk):
         Bb = B[b * block:(b + 1) * block]
-        e = eB[b * block * nao:(b * block + Bb.shape[0]) * nao].astype(np.float64)
-        st.append((np.abs(Bb).max(), float((Bb * Bb).sum()), e.sum(), float(len(e)), e.min(), e.max(),
-                   float(np.sum(e < e.max() - 20))))
-    st = np.array(st)
-    gmax, gss = st[:, 0].max(), st[:, 1].sum()
+        maxes.append(float(np.abs(Bb).max()))
+        sums.append(float(np.sum(Bb * Bb)))
+    gmax, gss = max(maxes), sum(sums)
     F = np.zeros((nblk, 16))
-    tiny = 1e-300
     for b in range(nblk):
-        mx, ss, es, cnt, emin, emax, small = st[b]
-        nP = min(block, naux - b * block)
-        F[b] = [np.log2(mx + tiny) / 32, 0.5 * np.log2(ss + tiny) / 32, es / max(cnt, 1) / 32, (emax - emin) / 32,
-                np.log10(tau) / 16, np.log10(dD + 1e-30) / 16, b / nblk, np.log2(nP) / 8, np.log2(nao) / 12,
-                np.log2(nocc) / 10, np.log2(ss / max(gss, tiny) + tiny) / 32, small / max(cnt, 1), s_rule / 8,
-                (np.log2(mx + tiny) - np.log2(gmax + tiny)) / 32, np.log10(dE + 1e-30) / 16, 1.0]
+        p0, p1 = b * block, min((b + 1) * block, naux)
+        e = np.asarray(eB[p0 * nao:p1 * nao], dtype=np.float64)
+        emax, emin = e.max(), e.min()
+        F[b, 0] = np.log2(maxes[b] + tiny) / 32
+        F[b, 1] = 0.5 * np.log2(sums[b] + tiny) / 32
+        F[b, 2] = e.mean() / 32
+        F[b, 3] = (emax - emin) / 32
+        F[b, 4] = np.log10(tau) / 16
+        F[b, 5] = np.log10(dD + 1e-30) / 16
+        F[b, 6] = b / nblk
+        F[b, 7] = np.log2(p1 - p0) / 8
+        F[b, 8] = np.log2(nao) / 12
+        F[b, 9] = np.log2(nocc) / 10
+        F[b, 10] = np.log2(sums[b] / max(gss, tiny) + tiny) / 32
+        F[b, 11] = np.count_nonzero(e < emax - 20) / len(e)
+        F[b, 12] = s_rule / 8
+        F[b, 13] = (np.log2(maxes[b] + tiny) - np.log2(gmax + tiny)) / 32
+        F[b, 14] = np.log10(dE + 1e-30) / 16
+        F[b, 15] = 1.0
     return F

@@ -13,7 +13,10 @@
 // The array lives on every GPU that loads this library until the process
 // exits.  Its device address is looked up once per device, with that device
 // current, on the first call made on that device.  That first call should
-// therefore come before any stream capture.  All calls share the array and it
+// therefore come before any stream capture.  The address is kept for the
+// life of the process: after cudaDeviceReset the cached address no longer
+// belongs to the device's new context, so a process that resets a device
+// must not call this entry point on that device again.  All calls share the array and it
 // keeps the contents of the last call; the status word is cleared at the start
 // of each call and every other byte that is read is written first.  Calls
 // whose GPU work overlaps (for example from two host threads on two streams)
@@ -58,13 +61,16 @@ extern "C" df_status df_emulated_gemm_static(const double *A, const double *B, i
                                              double *out, void *stream) {
   if (!A || !B || !out || M <= 0 || N <= 0 || K <= 0 || nslices < 1 || nslices > DF_S_MAX) return DF_ERR_ARG;
   const long long ld = ((long long)K + 7) / 8 * 8;
-  // carve the scratch: status word, exponents of A and B, digit planes of A and B
+  // A B^T with B == A (a Gram matrix): one split serves both sides, as in
+  // df_emulated_gemm, so only one operand's planes and exponents are carved
+  const bool same = A == B && M == N;
+  // carve the scratch: status word, exponents of A (and B), digit planes of A (and B)
   const size_t off_status = 0;
   const size_t off_ea = align256(off_status + sizeof(int));
   const size_t off_eb = align256(off_ea + sizeof(int) * (size_t)M);
-  const size_t off_ad = align256(off_eb + sizeof(int) * (size_t)N);
+  const size_t off_ad = same ? off_eb : align256(off_eb + sizeof(int) * (size_t)N);
   const size_t off_bd = align256(off_ad + sizeof(uint16_t) * (size_t)nslices * M * ld);
-  const size_t need = align256(off_bd + sizeof(uint16_t) * (size_t)nslices * N * ld);
+  const size_t need = same ? off_bd : align256(off_bd + sizeof(uint16_t) * (size_t)nslices * N * ld);
   if (need > kStaticScratchBytes) return DF_ERR_SCRATCH;
 
   void *base = nullptr;
@@ -73,14 +79,15 @@ extern "C" df_status df_emulated_gemm_static(const double *A, const double *B, i
   unsigned char *s = static_cast<unsigned char *>(base);
   int *status = reinterpret_cast<int *>(s + off_status);
   int *ea = reinterpret_cast<int *>(s + off_ea);
-  int *eb = reinterpret_cast<int *>(s + off_eb);
   uint16_t *Ad = reinterpret_cast<uint16_t *>(s + off_ad);
-  uint16_t *Bd = reinterpret_cast<uint16_t *>(s + off_bd);
+  int *eb = same ? ea : reinterpret_cast<int *>(s + off_eb);
+  uint16_t *Bd = same ? Ad : reinterpret_cast<uint16_t *>(s + off_bd);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e == cudaSuccess) e = df::launch_split_rows_bf16(A, M, K, K, nslices, ea, Ad, ld, (long long)M * ld, st);
-  if (e == cudaSuccess) e = df::launch_split_rows_bf16(B, N, K, K, nslices, eb, Bd, ld, (long long)N * ld, st);
+  if (e == cudaSuccess && !same)
+    e = df::launch_split_rows_bf16(B, N, K, K, nslices, eb, Bd, ld, (long long)N * ld, st);
   if (e != cudaSuccess) return DF_ERR_CUDA;
   CUtensorMap ta, tb;
   if (!df::make_tmap_bf16(&ta, Ad, K, M, nslices, ld, (long long)M * ld) ||

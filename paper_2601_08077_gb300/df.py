@@ -22,7 +22,7 @@ PHASES = ("split_C", "gemm1", "split_X", "gemm2", "reduce", "rho", "coulomb", "e
 
 _STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA or cuBLAS call failed", -3: "device allocation failed",
            -4: "metric not positive definite", -5: "bounded device wait ran out", -6: "result missed its tolerance",
-           -7: "call out of order"}
+           -7: "call out of order", -8: "problem exceeds the static scratch of df_emulated_gemm_static"}
 
 
 class DFError(RuntimeError):

@@ -2,6 +2,8 @@
 lookup and its source hash, the FLOP model."""
 import importlib.util
 import json
+
+import numpy as np
 import os
 import subprocess
 import sys
@@ -49,3 +51,26 @@ def test_recorded_traffic_is_tied_to_the_sources():
     else:
         assert got is None                          # stale record: reported as null, never reused
     assert b.recorded_traffic("slice_gemm (X = B C)", first["workload"], first["nslices"] + 1, 1) is None
+
+
+def test_oracle_gate_on_the_small_molecule():
+    """The bench's accuracy gate: the oracle's per-block K and J sum to the whole-molecule
+    build, an exact K passes, and a K off by 2e-10 max|K| fails."""
+    b = _bench()
+    sys.path.insert(0, ROOT)
+    from oracle import df_oracle as O
+    from paper_2601_08077_gb300 import inputs
+    w = inputs.SMALL
+    mol, B, C, D = inputs.make_inputs(w)
+    base, K, J, rho = b.oracle_reference(B, C, D, w)
+    assert base["kind"] == "oracle" and base["value"] > 0 and "all 3 auxiliary blocks" in base["sample"]
+    K_full = O.exchange(B, C)
+    J_full = O.coulomb(B, O.rho(B, D))
+    assert np.max(np.abs(K - K_full)) <= 1e-13 * np.max(np.abs(K_full))
+    assert np.max(np.abs(J - J_full)) <= 1e-13 * np.max(np.abs(J_full))
+    EJ, EK = O.energies(D, J, K)
+    g = b.oracle_gate(K_full, J_full, (EJ, 0.0, EK), K, J, D)
+    assert g["gate_vs_oracle"] and g["dE_vs_oracle"] < 1e-10
+    Kbad = K_full.copy()
+    Kbad[3, 5] += 2e-10 * np.max(np.abs(K_full))
+    assert not b.oracle_gate(Kbad, J_full, (EJ, 0.0, EK), K, J, D)["gate_vs_oracle"]

@@ -36,6 +36,52 @@ def test_mlp_forward_and_gradients_match_oracle(df):
     assert np.max(np.abs(g - g_ref)) <= 1e-5 + 1e-4 * np.max(np.abs(g_ref))
 
 
+def test_adam_steps_match_oracle(df):
+    """Three df_mlp_train_step calls against the oracle's Adam (beta 0.9 / 0.999, bias
+    correction) on the oracle's FP64 gradients, element by element.  The first update is
+    lr g / (|g| + eps) ~ lr sign(g), so an element whose gradient is within the FP32
+    gradient error of zero may take either sign: those get a bound of 2 lr per step, the
+    rest must agree to 2 % of lr per step."""
+    rng = np.random.default_rng(11)
+    theta0 = (M.init_params(4) + 0.05 * rng.standard_normal(M.N_PARAMS)).astype(np.float32)
+    X = rng.standard_normal((96, 16)).astype(np.float32)
+    y = rng.integers(0, 8, size=96)
+    net = df.MLP(theta0)
+    Xg = torch.from_numpy(X).cuda()
+    yg = torch.from_numpy(y.astype(np.int32)).cuda()
+    lr = 1e-3
+    th = theta0.astype(np.float64)
+    m = np.zeros(M.N_PARAMS)
+    v = np.zeros(M.N_PARAMS)
+    gmin = np.full(M.N_PARAMS, np.inf)
+    for t in (1, 2, 3):
+        g = M.gradients(th, X.astype(np.float64), y)
+        gmin = np.minimum(gmin, np.abs(g))
+        th, m, v = M.adam_step(th, g, m, v, t, lr)
+        net.train_step(Xg, yg, lr)
+        got = net.get_params().astype(np.float64)
+        sure = gmin > 1e-3 * np.max(np.abs(g))
+        diff = np.abs(got - th)
+        assert sure.sum() > 0.5 * M.N_PARAMS
+        assert np.max(diff[sure]) <= 0.02 * lr * t + 1e-7
+        assert np.max(diff) <= 2 * lr * t + 1e-7
+    # the parameters really moved by about lr per step (no update lost)
+    moved = np.abs(net.get_params().astype(np.float64) - theta0)
+    assert np.median(moved[sure]) > 0.5 * lr
+
+
+def test_block_features_of_hand_built_tensor(df):
+    """The library's features of the hand-built tensor whose 16 values per block are
+    worked out by hand in the oracle's pins (a ragged block of 2 functions included)."""
+    from test_oracle_mlp import hand_features, hand_tensor
+    B, _ = hand_tensor()
+    ctx = df.Context(2, 130, 4)
+    Bg = torch.from_numpy(B).cuda()
+    ctx.setup(Bg)
+    F = df.block_features(ctx, 4, 1e-10, 1e-4, 1e-8, 5).cpu().numpy()
+    assert np.allclose(F, hand_features(), rtol=0, atol=2e-7)
+
+
 def test_mlp_training_fits_a_small_set(df):
     rng = np.random.default_rng(6)
     X = rng.standard_normal((64, 16)).astype(np.float32)
