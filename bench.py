@@ -36,7 +36,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "DF K-build effective FP64 TFLOP/s, INT8-adaptive vs native FP64, max|dK|<=1e-10"
 UNIT = "TFLOP/s"
-LAUNCHES_PER_STEP = 9      # rho, coulomb, split C, GEMM1, split X, GEMM2, reduce, 2 energy kernels
+LAUNCHES_PER_STEP = 11     # rho, coulomb, 2 density-change kernels, split C, GEMM1, split X, GEMM2, reduce,
+                           # 2 energy kernels
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -49,12 +50,14 @@ def parse():
     ap.add_argument("--workload", choices=["small", "profile", "medium", "large", "batch", "sequence", "predictor", "scf",
                                                    "crt"],
                     default="large")
-    ap.add_argument("--size", choices=["small", "profile", "medium", "large"], default="medium",
-                    help="molecule of the sequence / predictor evaluation")
-    ap.add_argument("--train-molecules", type=int, default=48)
+    ap.add_argument("--size", choices=["small", "profile", "medium", "large"], default=None,
+                    help="molecule of the sequence / predictor evaluation (default: medium; predictor: large)")
+    ap.add_argument("--train-molecules", type=int, default=200)
     ap.add_argument("--batch-size", type=int, default=48)
     ap.add_argument("--nslices", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-records", action="store_true",
+                    help="skip the sequence, sweep and batch records that follow the timed steps")
     ap.add_argument("--aux-blocks", type=int, default=0,
                     help="keep only the first N 128-function auxiliary blocks of the workload (a smaller case of "
                          "the same kernels, for profiling); 0 keeps them all")
@@ -217,11 +220,18 @@ def run_batch(args):
     exchange builds in grouped persistent launches captured as one CUDA graph, against one
     native-FP64 build per molecule on the same GPU."""
     import torch
-    from paper_2601_08077_gb300 import build, df, inputs
+    from paper_2601_08077_gb300 import build
     build.build_all()
     torch.cuda.set_device(0)
-    ws = inputs.batch_workloads(args.batch_size)
-    s = args.nslices
+    return batch_record(args.batch_size, args.nslices, args.steps, args.warmup)
+
+
+def batch_record(n_mol, s, steps, warmup):
+    import types
+    import torch
+    from paper_2601_08077_gb300 import df, inputs
+    args = types.SimpleNamespace(steps=steps, warmup=warmup)
+    ws = inputs.batch_workloads(n_mol)
     t0 = time.perf_counter()
     ctxs, Bs, Cs, Ds = [], [], [], []
     for w in ws:
@@ -272,13 +282,65 @@ def run_batch(args):
     return {"metric": "batched DF J/K builds, molecules/s and effective FP64 TFLOP/s", "value": FK / (ms * 1e-3) / 1e12,
             "unit": UNIT, "molecules_per_s": len(ws) / (ms * 1e-3), "n_molecules": len(ws), "ms_per_batch": ms,
             "steps": args.steps, "warmup": args.warmup, "nslices": s, "autotune": {"ksplit_cap": choice[0],
-                                                                                 "order": choice[1]},
+                                                                                 "order": choice[1],
+                                                                                 "gemm1_tile": "256x128 CTA pair"
+                                                                                 if choice[2] else "128x128"},
             "fp64_per_molecule": {"ms_per_batch": ms64, "tflops": FK / (ms64 * 1e-3) / 1e12,
                                   "molecules_per_s": len(ws) / (ms64 * 1e-3)},
             "max_dK_rel_vs_fp64": worst, "generation_s": gen_s,
             "config": {"workload": "batch-%d-molecules-30to120-atoms" % len(ws), "nao": [w.nao for w in ws],
                        "naux_per_nao": 3, "nocc": "nao/5"},
             "clocks": clk.summary()}
+
+
+def sweep_record(reps=10):
+    """The fixed-slice sweep on the 120-atom molecule (nao 600, naux 1800, nocc 120): K at 3..8
+    slices per operand, throughput per count, max|dK| against the native FP64 build, |dE|
+    against FP64, and J against the CPU oracle (J does not depend on the count)."""
+    import torch
+    from oracle import df_oracle as O
+    from paper_2601_08077_gb300 import df, inputs
+    w = inputs.MEDIUM
+    mol = inputs.molecule(w.n_atoms, w.seed)
+    ctx = df.Context(w.nao, w.naux, w.nocc)
+    Bg = ctx.setup_integrals(torch.from_numpy(inputs.int3c(mol)).cuda(), torch.from_numpy(inputs.metric(mol)).cuda())
+    C = inputs.orbitals(mol.nao, w.nocc, w.seed + 1)
+    D = inputs.density(C)
+    Cg, Dg = torch.from_numpy(C).cuda(), torch.from_numpy(D).cuda()
+    J, rho = ctx.build_J(Dg)
+    K64 = ctx.build_K(Cg, 0)[0].clone()
+    E64 = ctx.energy(Dg, J, K64, rho)
+    kmax = float(K64.abs().max())
+    Jh = J.cpu().numpy()
+    J_ref = np.zeros_like(Jh)
+    for p0 in range(0, w.naux, 128):
+        Bb = Bg[p0:p0 + 128].cpu().numpy()
+        J_ref += O.coulomb(Bb, O.rho(Bb, D))
+    rows = []
+    for s in range(3, 9):
+        K = ctx.build_K(Cg, s)[0]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.build_K(Cg, s, K)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        E = ctx.energy(Dg, J, K, rho)
+        rows.append({"slices": s, "k_build_ms": ms, "tflops": flops_K(w) / (ms * 1e-3) / 1e12,
+                     "max_dK_rel_vs_fp64": float((K - K64).abs().max()) / kmax,
+                     "dE_vs_fp64": abs((E[0] + E[2]) - (E64[0] + E64[2]))})
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    ctx.build_K(Cg, 0, K64)
+    f1.record()
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    return {"workload": w.name, "per_slice_count": rows,
+            "max_dJ_rel_vs_oracle": float(np.max(np.abs(Jh - J_ref)) / np.max(np.abs(J_ref))),
+            "fp64_native": {"k_build_ms": ms64, "tflops": flops_K(w) / (ms64 * 1e-3) / 1e12}}
 
 
 def _molecule_on_device(w, order=False):
@@ -298,45 +360,74 @@ def run_sequence(args):
     from paper_2601_08077_gb300 import build, sequence
     build.build_all()
     torch.cuda.set_device(0)
-    w = workload(args.size)
+    w = workload(args.size or "medium")
     ctx, B, C = _molecule_on_device(w)
     orbs = sequence.orbital_sequence(C, 15, w.seed)
-    sequence.run(ctx, orbs[:2])                     # warm-up
-    rule = sequence.run(ctx, orbs)
-    rule8 = sequence.run(ctx, orbs, level0_slices=8)
-    fp64 = sequence.run(ctx, orbs, mode="fp64")
+    return sequence_record(ctx, w, orbs, full_fp64=True)
+
+
+def sequence_record(ctx, w, orbs, full_fp64=True):
+    """Rule (level 0 in FP64), rule with level 0 as 8 slices, and all-FP64 along the sequence.
+    full_fp64 False compares with FP64 at the last iteration only and times the FP64
+    sequence as one native iteration times the iteration count."""
+    from paper_2601_08077_gb300 import sequence
+    cache = {}
+    cmp = True if full_fp64 else "last"
+    sequence.run(ctx, orbs[:2], compare_fp64=False)     # warm-up
+    rule = sequence.run(ctx, orbs, fp64_cache=cache, compare_fp64=cmp)
+    rule8 = sequence.run(ctx, orbs, level0_slices=8, fp64_cache=cache, compare_fp64=cmp)
+    if full_fp64:
+        fp64 = sequence.run(ctx, orbs, mode="fp64", compare_fp64=False)
+        t_fp64 = sum(r["ms"] for r in fp64)
+        fp64_how = "measured, every iteration"
+    else:
+        one = sequence.run(ctx, orbs[:1], mode="fp64", compare_fp64=False)
+        t_fp64 = one[0]["ms"] * len(orbs)
+        fp64_how = "one native-FP64 iteration (J + K + energies) measured, times %d" % len(orbs)
     t_rule = sum(r["ms"] for r in rule)
     t_rule8 = sum(r["ms"] for r in rule8)
-    t_fp64 = sum(r["ms"] for r in fp64)
     FK = flops_K(w) * len(orbs)
     return {"metric": "adaptive-precision DF sequence (15 iterations, J + K + energies per iteration)",
-            "workload": w.name, "ms_total_rule": t_rule, "ms_total_fp64": t_fp64, "speedup": t_fp64 / t_rule,
-            "effective_tflops_rule": FK / (t_rule * 1e-3) / 1e12,
+            "workload": w.name, "ms_total_rule": t_rule, "ms_total_fp64": t_fp64, "fp64_timing": fp64_how,
+            "speedup": t_fp64 / t_rule, "effective_tflops_rule": FK / (t_rule * 1e-3) / 1e12,
             "level0_as_8_slices": {"ms_total": t_rule8, "speedup": t_fp64 / t_rule8,
                                    "effective_tflops": FK / (t_rule8 * 1e-3) / 1e12,
+                                   "levels": [r["level"] for r in rule8],
+                                   "slices": [r["slices"][0] for r in rule8],
                                    "dE_vs_fp64_final": rule8[-1]["dE_vs_fp64"],
                                    "max_dK_rel_final": rule8[-1]["max_dK_rel"]},
-            "levels": [r["level"] for r in rule], "slices": [r.get("slices") for r in rule],
+            "levels": [r["level"] for r in rule], "slices": [r["slices"][0] for r in rule],
             "ms_per_iteration": [round(r["ms"], 3) for r in rule],
-            "max_dK_rel": [r["max_dK_rel"] for r in rule], "dE_vs_fp64": [r["dE_vs_fp64"] for r in rule],
-            "density_change": [r["dnorm"] for r in rule], "E_final": rule[-1]["E"], "E_fp64_final": fp64[-1]["E"]}
+            "max_dK_rel": [r.get("max_dK_rel") for r in rule], "dE_vs_fp64": [r.get("dE_vs_fp64") for r in rule],
+            "density_change": [r["dnorm"] for r in rule], "E_final": rule[-1]["E"],
+            "E_fp64_final": rule[-1]["E_fp64"]}
 
 
 def run_predictor(args):
-    """Learned per-block slice counts: trained on generated molecules (labels from the method
-    against FP64), evaluated along the SCF-like sequence against the Table 1 rule."""
+    """The learned part as specified: a network trained on generated molecules of nao 100-600
+    (labels from the method against FP64: per level, the per-block counts with the fewest
+    slice pairs whose summed block errors stay within the rule's), then the 240-atom
+    sequence run by the library's learned mode (prediction, low-confidence fallback,
+    FP64-free bound check and recompute) against the same sequence under the rule."""
     import torch
     from paper_2601_08077_gb300 import build, inputs, predictor, sequence
     build.build_all()
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
     Fs, ys = [], []
-    for w in inputs.training_workloads(args.train_molecules):
+    opt_pairs, rule_pairs = 0, 0
+    ws = inputs.training_workloads(args.train_molecules)
+    for w in ws:
         ctx, B, C = _molecule_on_device(w, order=True)
-        F, y, _, _ = predictor.molecule_dataset(ctx, torch.from_numpy(C).cuda(), seed=w.seed)
+        F, y, err, kmax = predictor.molecule_dataset(ctx, torch.from_numpy(C).cuda(), seed=w.seed)
         Fs.append(F)
         ys.append(y)
+        nb = err.shape[0]
+        for lv, (tau, s_rule) in predictor.LEVELS.items():
+            rule_pairs += nb * predictor.pairs(s_rule)
+            opt_pairs += sum(predictor.pairs(int(s)) for s in predictor.labels_at_rule_accuracy(err, s_rule))
         del ctx, B
+        torch.cuda.empty_cache()
     F = torch.cat(Fs)
     y = torch.cat(ys)
     t_data = time.perf_counter() - t0
@@ -345,23 +436,35 @@ def run_predictor(args):
     hist = p.fit(F, y, steps=3000, lr=3e-3, batch=512)
     t_train = time.perf_counter() - t0
     acc = float((p.mlp.forward(F).argmax(1).to(torch.int32) == y).float().mean())
-    w = workload(args.size)
+    w = workload(args.size or "large")
     ctx, B, C = _molecule_on_device(w, order=True)
     orbs = sequence.orbital_sequence(C, 15, w.seed)
-    recs = sequence.run(ctx, orbs, mode="predictor", predictor=p, check_blocks=True)
-    rule = sequence.run(ctx, orbs)
-    wp = sum(r.get("work_pred", 0) for r in recs)
-    wr = sum(r.get("work_rule", 0) for r in recs)
-    wu = sum(r.get("work_uniform", 0) for r in recs)
-    return {"metric": "learned per-block slice counts vs the Table 1 rule", "train_molecules": args.train_molecules,
+    cache = {}
+    sequence.run(ctx, orbs[:2], compare_fp64=False)     # warm-up
+    rule = sequence.run(ctx, orbs, fp64_cache=cache)
+    p.attach(ctx)
+    sequence.run(ctx, orbs[:2], mode="learned", compare_fp64=False)
+    learned = sequence.run(ctx, orbs, mode="learned", fp64_cache=cache)
+    per_it = [{"level": a["level"], "pairs_rule": a["slice_pairs"], "pairs_learned": b["slice_pairs"],
+               "slices_learned": b["slices"], "recomputed": b["recomputed"], "low_confidence": b["low_confidence"],
+               "bound_ratio": b["bound_ratio"], "ms_rule": a["ms"], "ms_learned": b["ms"],
+               "max_dK_rel_rule": a.get("max_dK_rel"), "max_dK_rel_learned": b.get("max_dK_rel")}
+              for a, b in zip(rule, learned)]
+    return {"metric": "learned per-block slice counts vs the Table 1 rule (240-atom sequence)",
+            "train_molecules": len(ws), "train_nao": [min(x.nao for x in ws), max(x.nao for x in ws)],
             "train_samples": int(F.shape[0]), "train_seconds": t_train, "data_seconds": t_data,
-            "loss_first_last": [hist[0], hist[-1]], "train_accuracy": acc, "eval_workload": w.name,
-            "slice_pair_work": {"predictor": wp, "best_uniform_same_budget": wu, "rule_level_counts": wr},
-            "recomputed_blocks": sum(r.get("recomputed", 0) for r in recs),
-            "fallback_blocks": sum(r.get("fallbacks", 0) for r in recs),
-            "ms_predictor": sum(r["ms"] for r in recs), "ms_rule": sum(r["ms"] for r in rule),
-            "dE_vs_fp64_final": {"predictor": recs[-1]["dE_vs_fp64"], "rule": rule[-1]["dE_vs_fp64"]},
-            "levels": [r["level"] for r in recs]}
+            "loss_first_last": [hist[0], hist[-1]], "train_accuracy": acc,
+            "train_label_pairs_vs_rule": [opt_pairs, rule_pairs],
+            "eval_workload": w.name,
+            "slice_pairs": {"learned": sum(r["slice_pairs"] for r in learned),
+                            "rule": sum(r["slice_pairs"] for r in rule)},
+            "recomputed_blocks": sum(r["recomputed"] for r in learned),
+            "low_confidence_blocks": sum(r["low_confidence"] for r in learned),
+            "ms_learned": sum(r["ms"] for r in learned), "ms_rule": sum(r["ms"] for r in rule),
+            "dE_vs_fp64_final": {"learned": learned[-1]["dE_vs_fp64"], "rule": rule[-1]["dE_vs_fp64"]},
+            "max_dK_rel_worst": {"learned": max(r["max_dK_rel"] for r in learned if r["slices"][0]),
+                                 "rule": max(r["max_dK_rel"] for r in rule if r["slices"][0])},
+            "iterations": per_it}
 
 
 def run_scf(args):
@@ -373,7 +476,7 @@ def run_scf(args):
     from paper_2601_08077_gb300 import build, df, inputs, scf
     build.build_all()
     torch.cuda.set_device(0)
-    w = workload(args.size)
+    w = workload(args.size or "medium")
     mol = inputs.molecule(w.n_atoms, w.seed)
     Z = inputs.nuclear_charges(mol)
     S, T, V, En = inputs.one_electron(mol, Z)
@@ -421,7 +524,7 @@ def run_crt(args):
     from paper_2601_08077_gb300 import build, df, inputs
     build.build_all()
     torch.cuda.set_device(0)
-    w = workload(args.size)
+    w = workload(args.size or "medium")
     mol = inputs.molecule(w.n_atoms, w.seed)
     Bt = inputs.df_tensor_device(mol)
     nao, nocc = mol.nao, w.nocc
@@ -653,6 +756,21 @@ def main():
         out["accuracy"].update(oracle_gate(K_gate, J_gate, E_s, K_ref, J_ref, D))
         if not out["accuracy"]["gate_vs_oracle"]:
             print("bench: the run misses the accuracy gate against the oracle", file=sys.stderr)
+    if rank == 0 and not args.no_records and args.aux_blocks == 0 and w.name == workload("large").name:
+        # the other workloads of the metric, outside the timed region: the adaptive
+        # sequence on this molecule, then (memory freed) the fixed-slice sweep and the batch
+        from paper_2601_08077_gb300 import sequence
+        t0 = time.perf_counter()
+        orbs = sequence.orbital_sequence(C, 15, w.seed)
+        out["records"] = {"sequence": sequence_record(ctx, w, orbs, full_fp64=False)}
+        del ctx, Bg, K, J
+        if "Tg" in locals():
+            del Tg      # the same storage as Bg (B formed in place from the integrals)
+        torch.cuda.empty_cache()
+        out["records"]["sweep"] = sweep_record()
+        torch.cuda.empty_cache()
+        out["records"]["batch"] = batch_record(48, 5, 5, 2)
+        out["records"]["seconds"] = time.perf_counter() - t0
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -56,9 +56,13 @@ typedef struct df_ctx df_ctx;
 /* Statistics of one exchange build (host struct, optional). */
 typedef struct {
   int nblk;                 /* number of auxiliary blocks */
-  int slices[256];          /* slice count used per block (first 256 blocks) */
-  int recomputed;           /* blocks recomputed at more slices */
+  int slices[256];          /* slice count used per block (first 256 blocks; 0 = FP64) */
+  int recomputed;           /* learned mode: blocks the error-bound check raised and recomputed */
   int fallback;             /* 1 if the build ran in native FP64 */
+  int low_confidence;       /* learned mode: blocks that took the level's count for low confidence */
+  int level;                /* Table 1 level of an adaptive or learned build; -1 for fixed counts */
+  long long slice_pairs;    /* sum over blocks of s_b (s_b + 1) / 2 of the counts used */
+  double bound_ratio;       /* learned mode: sum_b beta_b(s_b) / sum_b beta_b(s_level) as run (<= 1) */
 } df_kstats;
 
 /* Create a context for one molecule: nao basis functions, naux auxiliary
@@ -104,14 +108,24 @@ df_status df_build_J(df_ctx *ctx, const double *D_dev, double *J_dev, double *rh
 
 /* Exchange build (Eqs. df-k-1, df-k-2, blocked as Eqs. df-k-blk-1/2).
  * C_dev [nao][nocc] (nocc <= nocc_max), K_dev [nao][nao] out (full,
- * symmetric).  nslices: 1..8 = INT8 emulation with that many slices per
- * operand for every block; 0 = native FP64 (cuBLAS DGEMM + DSYRK, the
- * comparison build).  stats may be NULL. */
+ * symmetric).  stats may be NULL.  nslices:
+ *   1..8  INT8 emulation with that many slices per operand for every block;
+ *   0     native FP64 (cuBLAS DGEMM + DSYRK, the comparison build);
+ *   -1    adaptive (Section 3.2, Table 1): the count of the context's current
+ *         level, as set by df_adaptive_reset / df_adaptive_next (level 0 runs
+ *         native FP64, or the df_adaptive_level0 count);
+ *   -2    learned: per-block counts for the current level from the network
+ *         attached with df_set_predictor, checked against the level's error
+ *         bound (df_set_predictor describes the check); blocks the check
+ *         raises are recomputed and counted in stats->recomputed.  At level 0
+ *         it runs as -1.  Synchronises `stream` (the predicted counts and the
+ *         check's exponents are read on the host); DF_ERR_STATE if no network
+ *         is attached. */
 df_status df_build_K(df_ctx *ctx, const double *C_dev, int nocc, int nslices, double *K_dev,
                      df_kstats *stats, void *stream);
 
 /* Exchange build with one slice count per auxiliary block (host array of
- * ceil(naux/128) entries, each 1..8).  Used by the learned predictor. */
+ * ceil(naux/128) entries, each 1..8), given by the caller; no check. */
 df_status df_build_K_blocks(df_ctx *ctx, const double *C_dev, int nocc, const int *slices_per_block,
                             double *K_dev, df_kstats *stats, void *stream);
 
@@ -255,10 +269,15 @@ df_status df_batch_build_K(df_batch *b, const double *const *C_dev, const int *n
 /* FP64 Coulomb build of every molecule (Eqs. df-j-1/2), graph-captured likewise;
  * rho goes to each context's internal buffer. */
 df_status df_batch_build_J(df_batch *b, const double *const *D_dev, double *const *J_dev, void *stream);
-/* Autotuner: times the K-split depth of the second GEMM (1, 2 or the
- * context's maximum) and the molecule order of the unit lists (as given, or
- * most expensive first) on this batch and keeps the fastest; choice[0] =
- * K-split cap, choice[1] = order.  Synchronises `stream`. */
+/* Autotuner: times, on this batch, every combination of the first GEMM's
+ * tile (CTA-pair 256 x 128 tiles with the (P, mu) rows on the MMA's M side,
+ * possible when every molecule's orbitals fit one 128-row tile, or
+ * single-CTA 128 x 128 tiles with the orbitals on M), the K-split cap of the
+ * second GEMM (1, 2, 4 or 8, at most the context's own split) and the
+ * molecule order of the unit lists (as given, or most expensive first), and
+ * keeps the fastest.  choice (host, 3 ints, may be NULL): [0] K-split cap,
+ * [1] order, [2] first-GEMM tile (1 pair, 0 single).  Synchronises
+ * `stream`. */
 df_status df_batch_autotune(df_batch *b, const double *const *C_dev, const int *nocc, int nslices,
                             double *const *K_dev, void *stream, int *choice);
 
@@ -292,6 +311,28 @@ df_status df_mlp_train_step(df_mlp *m, const float *X_dev, const int *y_dev, int
  * count. */
 df_status df_block_features(df_ctx *ctx, int nocc, double tau, double dD, double dE, int s_rule, float *F_dev,
                             void *stream);
+/* Attach the slice-count network to a context for df_build_K(nslices = -2)
+ * (the context keeps the pointer; NULL detaches; the caller keeps the network
+ * alive while attached).  At the current Table 1 level L (count s_L, printed
+ * accuracy tau_L) each build computes the 16 block features
+ * (df_block_features with tau_L, the density change measured by the last two
+ * df_build_J calls, the last relative energy change seen by
+ * df_adaptive_next, and s_L), runs the network, and takes for block b the
+ * most probable count s_b, or s_L when that probability is below min_conf
+ * (in (0, 1]).  After the first GEMM and the X split it checks, without any
+ * FP64 reference, the a-priori error bound of every block's K_b
+ *   beta_b(s) = kb_b 1.01 (s + 1) 2^(-8 s) (2^(2 E_b) + 2 nao 2^(F_b + E_c + E_b))
+ *               + kb_b 2^(2 E_b - 52)
+ * (kb_b = functions in the block x nocc, the contraction length; E_b the
+ * largest exponent of the block's X rows, F_b of its B rows, E_c of C's
+ * columns; the first term bounds the slice truncation of both GEMMs, the
+ * second the FP64 roundings): the counts pass if
+ * sum_b beta_b(s_b) <= sum_b beta_b(s_L), i.e. the learned build's bound is
+ * at most the rule's.  Otherwise the blocks with s_b < s_L are raised to s_L,
+ * largest beta_b(s_b) first, until it holds, and the first GEMM and the X
+ * split are run again with the raised counts. */
+df_status df_set_predictor(df_ctx *ctx, df_mlp *net, float min_conf);
+
 /* Labels: err_host [nblk][8] = max |K_b(s) - K_b(FP64)| of every block at
  * s = 1..8 (the emulated build against cuBLAS FP64, per block), *kmax_host =
  * max|K(FP64)|.  Runs s_max + 1 builds; synchronises. */

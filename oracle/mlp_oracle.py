@@ -2,8 +2,10 @@
 
 Plain NumPy FP64 restatement of the 16 -> 64 -> 64 -> 8 ReLU MLP with a
 softmax over the slice counts 1..8, its mean cross-entropy and its gradients
-by backpropagation, of the label rule (the least slice count whose per-block
-K error meets the block's share of the tolerance) and of the block features.
+by backpropagation, of the label rules (the least slice count whose per-block
+K error meets the block's share of a tolerance; the per-block counts of fewest
+slice pairs whose summed block errors stay within the rule's) and of the block
+features.
 The predictor is not in the paper; it extends the paper's closing suggestion
 (Section 5) of tying the emulation level to the change of the density matrix,
 with the per-block error budget read as an additive split of the tolerance.
@@ -110,6 +112,27 @@ def labels(err, kmax, tau, nblk):
         if len(ok):
             out[b] = ok[0] + 1
     return out
+
+
+def labels_at_rule_accuracy(err, s_rule):
+    """Per-block slice counts (1..8) with the fewest slice pairs sum_b s_b (s_b + 1) / 2
+    whose summed block errors stay within the rule's: sum_b err[b, s_b - 1] <=
+    sum_b err[b, s_rule - 1] (err[b, s - 1] = max|K_b(s) - K_b(FP64)|).  The
+    definition, by enumerating every assignment (tiny nblk only); ties go to the
+    smaller error sum, then to the lexicographically larger counts."""
+    import itertools
+    err = np.asarray(err, dtype=np.float64)
+    nblk = err.shape[0]
+    budget = float(np.sum(err[:, s_rule - 1]))
+    best = None
+    for combo in itertools.product(range(1, 9), repeat=nblk):
+        e = float(sum(err[b, combo[b] - 1] for b in range(nblk)))
+        if e > budget:
+            continue
+        key = (sum(s * (s + 1) // 2 for s in combo), e, tuple(-s for s in combo))
+        if best is None or key < best[0]:
+            best = (key, combo)
+    return np.array(best[1], dtype=np.int64)
 
 
 def block_features(B, eB, nocc, tau, dD, dE, s_rule, block=128):

@@ -25,6 +25,7 @@ struct df_batch {
   std::vector<df_ctx *> ctx;
   int nsplit_cap = 8;
   int order = 1;  // 0: as given, 1: most expensive first
+  int tile1 = 1;  // first GEMM: 1 CTA-pair 256 x 128 tiles when possible, 0 single-CTA 128 x 128
   bool graphs = true;
   // grouped-launch tables (device)
   df::SgParams *params1 = nullptr, *params2 = nullptr;
@@ -75,7 +76,7 @@ df_status build_tables(df_batch *b, const int *nocc) {
   b->nsplit.assign(n, 1);
   // the first GEMM runs on CTA pairs when every molecule's orbitals fit one tile
   // (the swapped layout; one slice count per molecule, so pairs may cross blocks)
-  b->pairs1 = true;
+  b->pairs1 = b->tile1 == 1;
   for (int i = 0; i < n; ++i) b->pairs1 = b->pairs1 && b->ctx[i]->pair_mode >= 1 && nocc[i] <= df::kTile;
   for (int k = 0; k < n; ++k) {
     const int i = ord[k];
@@ -290,27 +291,35 @@ df_status df_batch_autotune(df_batch *b, const double *const *C, const int *nocc
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // the first GEMM's CTA-pair tiles exist only when every molecule's orbitals fit one tile
+  bool pairs_possible = true;
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    pairs_possible = pairs_possible && b->ctx[i]->pair_mode >= 1 && nocc[i] <= df::kTile;
   float best = 1e30f;
-  int best_ns = b->nsplit_cap, best_ord = b->order;
+  int best_ns = b->nsplit_cap, best_ord = b->order, best_tile = pairs_possible ? 1 : 0;
   df_status r = DF_OK;
-  const int caps[3] = {1, 2, 8};
-  for (int ord = 0; ord < 2 && r == DF_OK; ++ord) {
-    for (int ci = 0; ci < 3 && r == DF_OK; ++ci) {
-      b->order = ord;
-      b->nsplit_cap = caps[ci];
-      b->tables_for_s = -1;
-      r = df_batch_build_K(b, C, nocc, nslices, K, stream);  // warm-up (and tables)
-      if (r != DF_OK) break;
-      cudaEventRecord(e0, st);
-      for (int rep = 0; rep < 2 && r == DF_OK; ++rep) r = df_batch_build_K(b, C, nocc, nslices, K, stream);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) r = DF_ERR_CUDA;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (r == DF_OK && ms < best) {
-        best = ms;
-        best_ns = caps[ci];
-        best_ord = ord;
+  const int caps[4] = {1, 2, 4, 8};
+  for (int tile = pairs_possible ? 1 : 0; tile >= 0 && r == DF_OK; --tile) {
+    for (int ord = 0; ord < 2 && r == DF_OK; ++ord) {
+      for (int ci = 0; ci < 4 && r == DF_OK; ++ci) {
+        b->tile1 = tile;
+        b->order = ord;
+        b->nsplit_cap = caps[ci];
+        b->tables_for_s = -1;
+        r = df_batch_build_K(b, C, nocc, nslices, K, stream);  // warm-up (and tables)
+        if (r != DF_OK) break;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2 && r == DF_OK; ++rep) r = df_batch_build_K(b, C, nocc, nslices, K, stream);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) r = DF_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r == DF_OK && ms < best) {
+          best = ms;
+          best_ns = caps[ci];
+          best_ord = ord;
+          best_tile = tile;
+        }
       }
     }
   }
@@ -318,12 +327,14 @@ df_status df_batch_autotune(df_batch *b, const double *const *C, const int *nocc
   cudaEventDestroy(e1);
   b->nsplit_cap = best_ns;
   b->order = best_ord;
+  b->tile1 = best_tile;
   b->tables_for_s = -1;
   b->graphs = graphs;
   drop_graph(b->exec_K);
   if (choice) {
     choice[0] = best_ns;
     choice[1] = best_ord;
+    choice[2] = best_tile;
   }
   return r;
 }

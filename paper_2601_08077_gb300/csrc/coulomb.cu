@@ -131,9 +131,53 @@ __global__ void energy_final_kernel(const double *__restrict__ part, int nblocks
   }
 }
 
+// Partial sums of (D - D_prev)^2 per block; D_prev == nullptr: no previous density.
+__global__ void __launch_bounds__(256) density_change_kernel(const double *__restrict__ D,
+                                                             const double *__restrict__ Dprev, long long n2,
+                                                             double *__restrict__ part) {
+  double a = 0.0;
+  if (Dprev) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+      const double d = D[i] - Dprev[i];
+      a = fma(d, d, a);
+    }
+  }
+  a = warp_sum(a);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+// ||D - D_prev||_F from the partials, or 1 when there is no previous density.
+__global__ void density_change_final_kernel(const double *__restrict__ part, int nblocks, bool have_prev,
+                                            double *__restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nblocks; ++i) s += part[i];
+    *out = have_prev ? sqrt(s) : 1.0;
+  }
+}
+
 }  // namespace
 
 constexpr int kEnergyBlocks = 296;
+
+cudaError_t launch_density_change(const double *D, double *Dprev, bool have_prev, long long n2, double *part,
+                                  double *out, cudaStream_t st) {
+  density_change_kernel<<<kDensityChangeBlocks, 256, 0, st>>>(D, have_prev ? Dprev : nullptr, n2, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  density_change_final_kernel<<<1, 32, 0, st>>>(part, kDensityChangeBlocks, have_prev, out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(Dprev, D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, st);
+}
 
 cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st) {
   rho_kernel<<<naux, 256, 0, st>>>(B, D, nao, rho);

@@ -231,15 +231,16 @@ long long xdigit_ld(int nocc) { return round_up((long long)kBlock * nocc, 64); }
 
 }  // namespace df
 
-namespace {
+namespace df {
 
-df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, double *K, df_kstats *stats,
-                           cudaStream_t st) {
+df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_planes, cudaStream_t st) {
   int smax = 0;
   for (int b = 0; b < c->nblk; ++b) {
     if (sb[b] < 1 || sb[b] > c->s_max) return record(c, DF_ERR_ARG);
     smax = sb[b] > smax ? sb[b] : smax;
   }
+  if (c_planes < smax) c_planes = smax;
+  if (c_planes > c->s_max) c_planes = c->s_max;
   df_status s = upload_slices(c, sb, st);
   if (s != DF_OK) return s;
   const int nao = c->nao, naux = c->naux;
@@ -247,7 +248,7 @@ df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, 
   const long long c_plane = (long long)c->nocc_max * c->ld_nao;
   {
     PhaseTimer t(c, DF_PHASE_SPLIT_C, st);
-    DF_TRY(c, df::launch_split_cols_bf16(C, nao, nocc, smax, c->eC, c->Cd, c->ld_nao, c_plane, st));
+    DF_TRY(c, df::launch_split_cols_bf16(C, nao, nocc, c_planes, c->eC, c->Cd, c->ld_nao, c_plane, st));
   }
   // 2. X^T = C^T B^T
   df::SgParams p;
@@ -266,6 +267,10 @@ df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, 
     DF_TRY(c, df::launch_split_xblocks(reinterpret_cast<const long long *>(c->X), naux, nao, nocc, smax, c->eB,
                                        c->eC, c->sblk, t1, c->eX, c->Xd, kb_ld, c->nblk, st));
   }
+  return DF_OK;
+}
+
+df_status k_back(df_ctx *c, int nocc, double *K, cudaStream_t st) {
   // 4. per-block K_b on upper tiles (exact int64 partials per K split)
   df::SgParams q2;
   CUtensorMap tx;
@@ -279,15 +284,42 @@ df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, 
     PhaseTimer t(c, DF_PHASE_REDUCE, st);
     df::ShiftTable tt;
     for (int q = 0; q <= 8; ++q) tt.v[q] = q2.shiftT[q];
-    DF_TRY(c, df::launch_kpart_reduce(c->Rp, c->eX, c->sblk, tt, nao, c->nblk, c->nsplit, K, st));
-  }
-  if (stats) {
-    stats->nblk = c->nblk;
-    for (int b = 0; b < c->nblk && b < 256; ++b) stats->slices[b] = sb[b];
-    stats->recomputed = 0;
-    stats->fallback = 0;
+    DF_TRY(c, df::launch_kpart_reduce(c->Rp, c->eX, c->sblk, tt, c->nao, c->nblk, c->nsplit, K, st));
   }
   return DF_OK;
+}
+
+int level_count(const df_ctx *c, int level) {
+  const bool fp64 = (level == 0 && c->level0_slices == 0) || (c->fp64_from >= 0 && level <= c->fp64_from);
+  return fp64 ? 0 : (level == 0 ? c->level0_slices : df_level_slices(level));
+}
+
+}  // namespace df
+
+namespace {
+
+void fill_stats(df_kstats *stats, const df_ctx *c, const int *sb, int level) {
+  if (!stats) return;
+  stats->nblk = c->nblk;
+  long long pairs = 0;
+  for (int b = 0; b < c->nblk; ++b) {
+    if (b < 256) stats->slices[b] = sb ? sb[b] : 0;
+    if (sb) pairs += (long long)sb[b] * (sb[b] + 1) / 2;
+  }
+  stats->recomputed = 0;
+  stats->fallback = sb ? 0 : 1;
+  stats->low_confidence = 0;
+  stats->level = level;
+  stats->slice_pairs = pairs;
+  stats->bound_ratio = sb ? 1.0 : 0.0;
+}
+
+df_status build_K_emulated(df_ctx *c, const double *C, int nocc, const int *sb, double *K, df_kstats *stats,
+                           cudaStream_t st, int level = -1) {
+  df_status s = df::k_front(c, C, nocc, sb, 0, st);
+  if (s == DF_OK) s = df::k_back(c, nocc, K, st);
+  if (s == DF_OK) fill_stats(stats, c, sb, level);
+  return s;
 }
 
 }  // namespace
@@ -376,8 +408,15 @@ df_status df_create(df_ctx **out, int nao, int naux, int nocc_max, int s_max) {
   if (e == cudaSuccess) e = alloc(c, &c->E, (size_t)4);
   if (e == cudaSuccess) e = alloc(c, &c->sblk, (size_t)c->nblk);
   if (e == cudaSuccess) e = alloc(c, &c->status, (size_t)1);
+  if (e == cudaSuccess) e = alloc(c, &c->Dprev, (size_t)nao * nao);
+  if (e == cudaSuccess) e = alloc(c, &c->dD, (size_t)1);
+  if (e == cudaSuccess) e = alloc(c, &c->dD_part, (size_t)df::kDensityChangeBlocks);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&c->sblk_host), sizeof(int) * c->nblk);
   if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    const double one = 1.0;  // no previous density yet: the density-change feature reads 1
+    e = cudaMemcpy(c->dD, &one, sizeof(double), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(c->sblk, 0, sizeof(int) * c->nblk);
   if (e == cudaSuccess) std::memset(c->sblk_host, 0, sizeof(int) * c->nblk);
   if (e != cudaSuccess) {
@@ -405,6 +444,14 @@ void df_destroy(df_ctx *c) {
   cudaFree(c->E);
   cudaFree(c->sblk);
   cudaFree(c->status);
+  cudaFree(c->Dprev);
+  cudaFree(c->dD);
+  cudaFree(c->dD_part);
+  cudaFree(c->lF);
+  cudaFree(c->lprobs);
+  cudaFree(c->lpick);
+  cudaFree(c->lexp);
+  if (c->lhost) cudaFreeHost(c->lhost);
   cudaFree(c->bstats);
   cudaFree(c->perm);
   if (c->sblk_host) cudaFreeHost(c->sblk_host);
@@ -474,9 +521,11 @@ df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host,
     }
     if (!c->perm) DF_TRY(c, cudaMalloc(&c->perm, sizeof(int) * c->naux));
     DF_TRY(c, cudaMemcpy(c->perm, perm_host, sizeof(int) * c->naux, cudaMemcpyHostToDevice));
+    c->perm_h.assign(perm_host, perm_host + c->naux);
   } else if (c->perm) {
     cudaFree(c->perm);
     c->perm = nullptr;
+    c->perm_h.clear();
   }
   if (c->bstats) {
     cudaFree(c->bstats);
@@ -504,28 +553,37 @@ df_status df_build_J(df_ctx *c, const double *D, double *J, double *rho, void *s
   }
   if (rho && rho != c->rho)
     DF_TRY(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * c->naux, cudaMemcpyDeviceToDevice, st));
+  // the density change since the last Coulomb build (an input of the learned slice counts)
+  DF_TRY(c, df::launch_density_change(D, c->Dprev, c->have_Dprev, (long long)c->nao * c->nao, c->dD_part, c->dD, st));
+  c->have_Dprev = true;
   return DF_OK;
 }
 
 df_status df_build_K(df_ctx *c, const double *C, int nocc, int nslices, double *K, df_kstats *stats, void *stream) {
-  if (!c || !C || !K || nocc <= 0 || nocc > c->nocc_max || nslices < 0 || nslices > c->s_max)
+  if (!c || !C || !K || nocc <= 0 || nocc > c->nocc_max || nslices < -2 || nslices > c->s_max)
     return record(c, DF_ERR_ARG);
   if (!c->ready) return record(c, DF_ERR_STATE);
   cudaStream_t st = as_stream(stream);
+  int level = -1;
+  if (nslices == -2 && c->level > 0) {
+    if (!c->pred) return record(c, DF_ERR_STATE);
+    return df::build_K_learned(c, C, nocc, K, stats, st);
+  }
+  if (nslices < 0) {
+    // the adaptive rule's count for the current level (learned mode at level 0 likewise)
+    level = c->level;
+    nslices = df::level_count(c, level);
+    if (nslices > c->s_max) return record(c, DF_ERR_ARG);
+  }
   if (nslices == 0) {
     df_status s = build_K_fp64(c, C, nocc, K, st);
-    if (stats && s == DF_OK) {
-      stats->nblk = c->nblk;
-      for (int b = 0; b < c->nblk && b < 256; ++b) stats->slices[b] = 0;
-      stats->recomputed = 0;
-      stats->fallback = 1;
-    }
+    if (s == DF_OK) fill_stats(stats, c, nullptr, level);
     return s;
   }
   int sb[4096];
   if (c->nblk > 4096) return record(c, DF_ERR_ARG);
   for (int b = 0; b < c->nblk; ++b) sb[b] = nslices;
-  return build_K_emulated(c, C, nocc, sb, K, stats, st);
+  return build_K_emulated(c, C, nocc, sb, K, stats, st, level);
 }
 
 df_status df_build_K_blocks(df_ctx *c, const double *C, int nocc, const int *slices, double *K, df_kstats *stats,
@@ -554,6 +612,7 @@ df_status df_adaptive_reset(df_ctx *c, int fp64_from_level) {
   c->level = 4;
   c->iter = 0;
   c->E_prev = 0.0;
+  c->dE_last = 1.0;
   c->fp64_from = fp64_from_level;
   return DF_OK;
 }
@@ -568,14 +627,14 @@ df_status df_adaptive_next(df_ctx *c, double energy, int *level_out, int *nslice
   if (!c || !level_out || !nslices_out) return DF_ERR_ARG;
   if (c->iter > 0 && energy != 0.0) {
     const double dE = std::fabs((energy - c->E_prev) / energy);
+    c->dE_last = dE;
     const int lv = df_level_for(dE);
     if (lv < c->level) c->level = lv;  // precision never drops
   }
   c->E_prev = energy;
   c->iter += 1;
   *level_out = c->level;
-  const bool fp64 = (c->level == 0 && c->level0_slices == 0) || (c->fp64_from >= 0 && c->level <= c->fp64_from);
-  *nslices_out = fp64 ? 0 : (c->level == 0 ? c->level0_slices : df_level_slices(c->level));
+  *nslices_out = df::level_count(c, c->level);
   return DF_OK;
 }
 

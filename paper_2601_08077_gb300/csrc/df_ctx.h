@@ -28,6 +28,7 @@ struct df_ctx {
   int *status = nullptr;
   double *bstats = nullptr;  // static per-block statistics for the predictor's features
   int *perm = nullptr;       // exchange-path order of the auxiliary functions (P' -> P), or null
+  std::vector<int> perm_h;   // host copy of perm (empty: natural order)
   int64_t bytes = 0;
   df_status last = DF_OK;
   cublasHandle_t cublas = nullptr;
@@ -40,6 +41,20 @@ struct df_ctx {
   // adaptive controller (Section 3.2)
   int level = 4, iter = 0, fp64_from = -1, level0_slices = 0;
   double E_prev = 0.0;
+  double dE_last = 1.0;      // last relative energy change seen by df_adaptive_next (1 before any)
+  // density change between successive df_build_J calls (a predictor feature)
+  double *Dprev = nullptr;   // [nao][nao] the density of the last df_build_J
+  double *dD = nullptr;      // device scalar ||D - D_prev||_F (1 before any previous density)
+  double *dD_part = nullptr; // partial sums of the reduction
+  bool have_Dprev = false;
+  // learned slice counts (df_set_predictor; the network's kernels live in mlp.cu)
+  df_mlp *pred = nullptr;
+  float min_conf = 0.6f;
+  float *lF = nullptr;       // [nblk][16] features
+  float *lprobs = nullptr;   // [nblk][8] class probabilities
+  int *lpick = nullptr;      // [2 nblk] picked counts, low-confidence flags
+  int *lexp = nullptr;       // [2 nblk + 1] per block max eX, max eB; then max eC
+  int *lhost = nullptr;      // pinned mirror of lpick / lexp
 };
 
 
@@ -55,4 +70,20 @@ df_status ctx_upload_slices(df_ctx *c, const int *sb, cudaStream_t st);
 bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb, int swap = 1);
 bool gemm2_setup(df_ctx *c, int nocc, int nsplit, SgParams &q2, CUtensorMap &tx);
 long long xdigit_ld(int nocc);
+// The two halves of an emulated exchange build with per-block counts sb:
+// the front uploads sb, splits C into c_planes digit planes (>= max sb), runs
+// the first GEMM and the X split; the back runs the second GEMM and the
+// reduce into K.  Both asynchronous on st.
+df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_planes, cudaStream_t st);
+df_status k_back(df_ctx *c, int nocc, double *K, cudaStream_t st);
+// The slice count run at a Table 1 level under the context's controller
+// settings (0 = native FP64).
+int level_count(const df_ctx *c, int level);
+// The learned-mode exchange build (mlp.cu): predicted per-block counts for the
+// context's current level, checked against the level's error bound.
+df_status build_K_learned(df_ctx *c, const double *C, int nocc, double *K, df_kstats *stats, cudaStream_t st);
+// Launch of ||D - D_prev||_F into c->dD (1 when there is no previous density)
+// and the copy D -> D_prev (coulomb.cu).
+cudaError_t launch_density_change(const double *D, double *Dprev, bool have_prev, long long n2, double *part,
+                                  double *out, cudaStream_t st);
 }  // namespace df

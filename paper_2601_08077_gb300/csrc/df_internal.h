@@ -40,6 +40,9 @@ enum SgLayout : int {
 
 constexpr int kCrtMaxModuli = 16;
 
+// Blocks of the density-change reduction ||D - D_prev||_F (df_build_J).
+constexpr int kDensityChangeBlocks = 152;
+
 // Row splits give a whole 256-thread block to each row at least this wide
 // (fewer, longer rows: the second exchange GEMM's operands), else a warp.
 constexpr int kWideRow = 2048;
@@ -63,8 +66,10 @@ struct SgParams {
   long long *raw;
   int *status;              // device status word (DF_ERR_TIMEOUT bits)
   // CTA-pair mode: two CTAs of a cluster take two tiles that share their
-  // B-side operand, which each loads half of and multicasts to both.
-  // Work is then counted in tile pairs (npairs); the host sets both.
+  // B-side operand; each CTA loads its own A tile and one of the two stacked
+  // B tiles into its own shared memory (both copies complete on the first
+  // CTA's barrier), and one M = 256 MMA reads both CTAs' tiles.  Work is
+  // then counted in tile pairs (npairs); the host sets both.
   int pair;
   int npairs;
   int crt_mod[kCrtMaxModuli];  // kModeMod: the modulus of each plane

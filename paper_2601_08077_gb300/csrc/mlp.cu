@@ -7,6 +7,8 @@
 //   W1 [64][16], b1 [64], W2 [64][64], b2 [64], W3 [8][64], b3 [8].
 #include "df_ctx.h"
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -215,10 +217,14 @@ __global__ void __launch_bounds__(256) block_stats_kernel(const double *__restri
 }
 
 // 16 features per block from the static statistics and the iteration's scalars.
+// dD_dev, when given, replaces dD (the density change measured on the device).
 __global__ void block_features_kernel(const double *__restrict__ stats, int nblk, int naux, int nao, int nocc,
-                                      double tau, double dD, double dE, int s_rule, float *__restrict__ F) {
+                                      double tau, double dD, const double *__restrict__ dD_dev, double dE,
+                                      int s_rule, float *__restrict__ F) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblk) return;
+  if (dD_dev) dD = *dD_dev;
+  if (!(dD >= 0.0 && dD <= 1e300)) dD = 1.0;  // a non-finite change reads as "large", never as NaN
   double gmax = 0.0, gss = 0.0;
   for (int k = 0; k < nblk; ++k) {
     gmax = fmax(gmax, stats[k * 8 + 0]);
@@ -263,6 +269,65 @@ __global__ void block_error_kernel(const long long *__restrict__ Rp, const int *
   const int k = eX[b * nao + mu] + eX[b * nao + nu] - 14 - 8 * (s - 1) + T.v[s];
   const double d = fabs(df::ldexp_i64(R, k) - K64[(long long)b * bs + (long long)mu * nao + nu]);
   atomicMax(&err[b], (unsigned long long)__double_as_longlong(d));
+}
+
+// Learned counts: per block the most probable class + 1, or s_rule when that
+// probability is below min_conf (flag set); counts capped at s_max.
+__global__ void pick_slices_kernel(const float *__restrict__ probs, int nblk, float min_conf, int s_rule, int s_max,
+                                   int *__restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  int best = 0;
+  float pb = probs[b * kOut];
+  for (int c = 1; c < kOut; ++c)
+    if (probs[b * kOut + c] > pb) {
+      pb = probs[b * kOut + c];
+      best = c;
+    }
+  const bool low = pb < min_conf;
+  const int s = low ? s_rule : best + 1;
+  out[b] = s < s_max ? s : s_max;
+  out[nblk + b] = low ? 1 : 0;
+}
+
+// Exponents of the error-bound check: out[b] = max_mu eX[b, mu], out[nblk + b]
+// = max eB over the block's (P, mu) rows, out[2 nblk] = max eC.  One CTA per
+// block (plus one for eC).
+__global__ void __launch_bounds__(256) check_exponents_kernel(const int *__restrict__ eX, const int *__restrict__ eB,
+                                                              const int *__restrict__ eC, int nblk, int nao, int naux,
+                                                              int nocc, int *__restrict__ out) {
+  const int b = blockIdx.x;
+  int ex = INT_MIN, eb = INT_MIN;
+  if (b < nblk) {
+    for (int mu = threadIdx.x; mu < nao; mu += blockDim.x) ex = max(ex, eX[b * nao + mu]);
+    const long long r0 = (long long)b * df::kBlock * nao;
+    const long long r1 = (long long)min(naux, (b + 1) * df::kBlock) * nao;
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) eb = max(eb, eB[r]);
+  } else {
+    for (int i = threadIdx.x; i < nocc; i += blockDim.x) ex = max(ex, eC[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+    eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+  }
+  __shared__ int rx[8], rb[8];
+  if ((threadIdx.x & 31) == 0) {
+    rx[threadIdx.x >> 5] = ex;
+    rb[threadIdx.x >> 5] = eb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) {
+      ex = max(ex, rx[w]);
+      eb = max(eb, rb[w]);
+    }
+    if (b < nblk) {
+      out[b] = ex;
+      out[nblk + b] = eb;
+    } else {
+      out[2 * nblk] = ex;
+    }
+  }
 }
 
 }  // namespace
@@ -372,7 +437,7 @@ df_status df_block_features(df_ctx *c, int nocc, double tau, double dD, double d
     if (cudaGetLastError() != cudaSuccess) return DF_ERR_CUDA;
   }
   block_features_kernel<<<(c->nblk + 127) / 128, 128, 0, st>>>(c->bstats, c->nblk, c->naux, c->nao, nocc, tau, dD,
-                                                               dE, s_rule, F);
+                                                               nullptr, dE, s_rule, F);
   return cudaGetLastError() == cudaSuccess ? DF_OK : DF_ERR_CUDA;
 }
 
@@ -392,14 +457,33 @@ df_status df_block_errors(df_ctx *c, const double *C, int nocc, double *err_host
   // FP64 reference: X^T by cuBLAS (as in the native build), then K_b = Xt_b^T Xt_b per block
   if (r == DF_OK) r = df_build_K(c, C, nocc, 0, Kfull, nullptr, stream);
   if (r == DF_OK) {
+    // the FP64 build leaves X^T [mu][(P, i)] in the natural P order; a block of
+    // the exchange order (df_setup_ordered) gathers its functions' columns first
     const double one = 1.0, zero = 0.0;
     const long long ldx = (long long)c->naux * nocc;
+    const long long kbw = (long long)df::kBlock * nocc;
+    double *Xg = nullptr;
+    if (!c->perm_h.empty() && cudaMalloc(&Xg, sizeof(double) * nao * kbw) != cudaSuccess) r = DF_ERR_OOM;
     for (int b = 0; b < nblk && r == DF_OK; ++b) {
       const int nP = (b + 1) * df::kBlock <= c->naux ? df::kBlock : c->naux - b * df::kBlock;
-      if (cublasDgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, nao, nao, nP * nocc, &one,
-                      c->X + (long long)b * df::kBlock * nocc, (int)ldx, c->X + (long long)b * df::kBlock * nocc,
-                      (int)ldx, &zero, K64 + (long long)b * bs, nao) != CUBLAS_STATUS_SUCCESS)
+      const double *Xb = c->X + (long long)b * df::kBlock * nocc;
+      long long ld = ldx;
+      if (Xg) {
+        for (int j = 0; j < nP && r == DF_OK; ++j)
+          if (cudaMemcpy2DAsync(Xg + (long long)j * nocc, sizeof(double) * kbw,
+                                c->X + (long long)c->perm_h[b * df::kBlock + j] * nocc, sizeof(double) * ldx,
+                                sizeof(double) * nocc, nao, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            r = DF_ERR_CUDA;
+        Xb = Xg;
+        ld = kbw;
+      }
+      if (r == DF_OK && cublasDgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, nao, nao, nP * nocc, &one, Xb, (int)ld, Xb,
+                                    (int)ld, &zero, K64 + (long long)b * bs, nao) != CUBLAS_STATUS_SUCCESS)
         r = DF_ERR_CUDA;
+    }
+    if (Xg) {
+      cudaStreamSynchronize(st);
+      cudaFree(Xg);
     }
   }
   if (r == DF_OK && kmax_host) {
@@ -450,3 +534,139 @@ df_status df_block_errors(df_ctx *c, const double *C, int nocc, double *err_host
 }
 
 }  // extern "C"
+
+namespace {
+
+// Table 1's printed accuracy per level (levels 1..4), the tolerance feature.
+constexpr double kLevelTau[5] = {0.0, 7.1e-15, 1.8e-12, 4.7e-10, 1.2e-7};
+
+// log2 of the a-priori error bound beta_b(s) of block b's K_b (see
+// df_set_predictor): kb 1.01 (s+1) 2^(-8s) (2^(2E) + 2 nao 2^(F+Ec+E)) + kb 2^(2E-52).
+double log2_bound(int s, double kb, int nao, int E, int F, int Ec) {
+  const double a = 2.0 * E, b = 1.0 + std::log2((double)nao) + F + Ec + E;
+  const double hi = std::max(a, b);
+  const double trunc = std::log2(1.01 * (s + 1)) - 8.0 * s + hi + std::log2(std::exp2(a - hi) + std::exp2(b - hi));
+  const double round = a - 52.0;
+  const double top = std::max(trunc, round);
+  return std::log2(kb) + top + std::log2(std::exp2(trunc - top) + std::exp2(round - top));
+}
+
+df_status cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return DF_OK;
+  return e == cudaErrorMemoryAllocation ? DF_ERR_OOM : DF_ERR_CUDA;
+}
+
+}  // namespace
+
+namespace df {
+
+df_status build_K_learned(df_ctx *c, const double *C, int nocc, double *K, df_kstats *stats, cudaStream_t st) {
+  const int level = c->level;
+  const int s_rule = level_count(c, level);
+  if (level < 1 || level > 4 || s_rule < 1 || s_rule > c->s_max) return DF_ERR_ARG;
+  const int nblk = c->nblk;
+  cudaError_t e = cudaSuccess;
+  if (!c->lF) e = cudaMalloc(&c->lF, sizeof(float) * 16 * nblk);
+  if (e == cudaSuccess && !c->lprobs) e = cudaMalloc(&c->lprobs, sizeof(float) * kOut * nblk);
+  if (e == cudaSuccess && !c->lpick) e = cudaMalloc(&c->lpick, sizeof(int) * 2 * nblk);
+  if (e == cudaSuccess && !c->lexp) e = cudaMalloc(&c->lexp, sizeof(int) * (2 * nblk + 1));
+  if (e == cudaSuccess && !c->lhost) e = cudaMallocHost(&c->lhost, sizeof(int) * (2 * nblk + 1));
+  if (e == cudaSuccess && !c->bstats) {
+    e = cudaMalloc(&c->bstats, sizeof(double) * 8 * nblk);
+    if (e == cudaSuccess) {
+      block_stats_kernel<<<nblk, 256, 0, st>>>(c->B, c->eB, c->perm, c->naux, c->nao, c->bstats);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) return cuda_err(e);
+  // 1. features -> network -> counts (with the low-confidence fallback)
+  block_features_kernel<<<(nblk + 127) / 128, 128, 0, st>>>(c->bstats, nblk, c->naux, c->nao, nocc,
+                                                            kLevelTau[level], 0.0, c->dD, c->dE_last, s_rule, c->lF);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    mlp_forward_kernel<<<(nblk + kRowsPerBlock - 1) / kRowsPerBlock, 256, 0, st>>>(c->pred->P, c->lF, nblk,
+                                                                                     c->lprobs);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    pick_slices_kernel<<<(nblk + 127) / 128, 128, 0, st>>>(c->lprobs, nblk, c->min_conf, s_rule, c->s_max,
+                                                           c->lpick);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->lhost, c->lpick, sizeof(int) * 2 * nblk, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(e);
+  std::vector<int> sb(c->lhost, c->lhost + nblk);
+  int low = 0;
+  for (int b = 0; b < nblk; ++b) low += c->lhost[nblk + b];
+  // 2. first GEMM and X split at the predicted counts (C split deep enough for s_rule)
+  df_status r = k_front(c, C, nocc, sb.data(), s_rule, st);
+  if (r != DF_OK) return r;
+  // 3. the error-bound check from the exponents
+  check_exponents_kernel<<<nblk + 1, 256, 0, st>>>(c->eX, c->eB, c->eC, nblk, c->nao, c->naux, nocc, c->lexp);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->lhost, c->lexp, sizeof(int) * (2 * nblk + 1), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(e);
+  const int Ec = c->lhost[2 * nblk];
+  std::vector<double> lb_rule(nblk), lb(nblk);
+  double ref = -INFINITY;
+  for (int b = 0; b < nblk; ++b) {
+    const int nP = std::min(kBlock, c->naux - b * kBlock);
+    const double kb = (double)nP * nocc;
+    lb_rule[b] = log2_bound(s_rule, kb, c->nao, c->lhost[b], c->lhost[nblk + b], Ec);
+    lb[b] = log2_bound(sb[b], kb, c->nao, c->lhost[b], c->lhost[nblk + b], Ec);
+    ref = std::max(ref, lb_rule[b]);
+  }
+  // sums of 2^(log2 bound - ref), all <= nblk
+  auto total = [&](const std::vector<double> &v) {
+    double t = 0.0;
+    for (double x : v) t += std::exp2(x - ref);
+    return t;
+  };
+  const double budget = total(lb_rule);
+  double have = total(lb);
+  int raised = 0;
+  while (have > budget * (1.0 + 1e-12)) {
+    int pick = -1;
+    for (int b = 0; b < nblk; ++b)
+      if (sb[b] < s_rule && (pick < 0 || lb[b] > lb[pick])) pick = b;
+    if (pick < 0) break;  // cannot happen: every block at >= s_rule meets the budget
+    sb[pick] = s_rule;
+    lb[pick] = lb_rule[pick];
+    ++raised;
+    have = total(lb);
+  }
+  if (raised) {
+    // 4. recompute the first GEMM and the X split with the raised counts
+    r = k_front(c, C, nocc, sb.data(), s_rule, st);
+    if (r != DF_OK) return r;
+  }
+  r = k_back(c, nocc, K, st);
+  if (r != DF_OK) return r;
+  if (stats) {
+    stats->nblk = nblk;
+    long long pairs = 0;
+    for (int b = 0; b < nblk; ++b) {
+      if (b < 256) stats->slices[b] = sb[b];
+      pairs += (long long)sb[b] * (sb[b] + 1) / 2;
+    }
+    stats->recomputed = raised;
+    stats->fallback = 0;
+    stats->low_confidence = low;
+    stats->level = level;
+    stats->slice_pairs = pairs;
+    stats->bound_ratio = have / budget;
+  }
+  return DF_OK;
+}
+
+}  // namespace df
+
+extern "C" df_status df_set_predictor(df_ctx *c, df_mlp *net, float min_conf) {
+  if (!c || !(min_conf > 0.f && min_conf <= 1.f)) return DF_ERR_ARG;
+  c->pred = net;
+  c->min_conf = min_conf;
+  return DF_OK;
+}

@@ -8,8 +8,11 @@
 //
 // All of it is integer arithmetic on the FP64 bit patterns.  The digits feed
 // the tensor cores as BF16 (every integer in [-256, 256] is exact in BF16).
-// These kernels are HBM-bound: each reads its FP64 input once from DRAM (the
-// second pass over a row hits L1/L2) and writes s bytes-worth of digits.
+// These kernels are HBM-bound: each reads its FP64 input and writes s
+// digits per value, in two passes over a row (its maximum, then the digits).
+// For the B and C splits the second pass mostly hits L1/L2; the X split's
+// rows (128 functions x nocc values, up to 256 KB) are mostly re-read from
+// DRAM.
 #include "df_internal.h"
 
 #include <climits>
@@ -169,10 +172,10 @@ __global__ void split_cols_bf16_kernel(const double *__restrict__ C, int nrows, 
 // X = fl64(R 2^k), k = -14 - 8(s_b - 1) + T(s_b) + eC[i] + eB[(P, mu)], the
 // one rounding of the emulated product, and splits it.  (Doing the rounding
 // here keeps the GEMM's epilogue short; it measured 18% faster that way.)
-// The first pass finds max|X| (R from DRAM), the second re-reads the row
-// (256 KB at most) and writes the digits.  Two consecutive orbitals per
-// thread (16-byte loads, 4-byte stores) when nocc is even, four loads in
-// flight per thread in the first pass.
+// The first pass finds the row's largest |X| from exact magnitude keys, the
+// second re-reads the row (256 KB at most, mostly from DRAM) and writes the
+// digits.  Two consecutive orbitals per thread (16-byte loads, 4-byte stores)
+// when nocc is even, four loads in flight per thread in the first pass.
 constexpr int kSplitXThreads = 256;
 constexpr int kP1 = 4;  // loads in flight per thread in the first pass (8 measured slower)
 
@@ -418,8 +421,8 @@ cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int ns
 }
 
 cudaError_t launch_split_xblocks(const long long *R, int naux, int nao, int nocc, int nslices, const int *eB,
-                                 const int *eC, const int *s_blk, const ShiftTable &T1, int *eX, uint16_t *Xd,
-                                 long long kb_ld, int nblk, cudaStream_t st) {
+                                 const int *eC, const int *s_blk, const ShiftTable &T1,
+                                 int *eX, uint16_t *Xd, long long kb_ld, int nblk, cudaStream_t st) {
   const size_t sm = sizeof(int) * (size_t)(kBlock + nocc);
   static size_t attr = 48 * 1024;
   if (sm > attr) {

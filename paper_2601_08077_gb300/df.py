@@ -31,9 +31,20 @@ class DFError(RuntimeError):
         self.status = status
 
 
+ADAPTIVE = -1  # df_build_K: the count of the context's current Table 1 level
+LEARNED = -2   # df_build_K: per-block counts from the attached network, checked
+
+
 class KStats(ctypes.Structure):
     _fields_ = [("nblk", ctypes.c_int), ("slices", ctypes.c_int * 256), ("recomputed", ctypes.c_int),
-                ("fallback", ctypes.c_int)]
+                ("fallback", ctypes.c_int), ("low_confidence", ctypes.c_int), ("level", ctypes.c_int),
+                ("slice_pairs", ctypes.c_longlong), ("bound_ratio", ctypes.c_double)]
+
+    def as_dict(self):
+        n = min(self.nblk, 256)
+        return {"nblk": self.nblk, "slices": list(self.slices[:n]), "recomputed": self.recomputed,
+                "fallback": self.fallback, "low_confidence": self.low_confidence, "level": self.level,
+                "slice_pairs": self.slice_pairs, "bound_ratio": self.bound_ratio}
 
 
 _lib = None
@@ -96,6 +107,7 @@ def lib():
         L.df_mlp_train_step.argtypes = [P, P, P, I, ctypes.c_float, FP, V]
         L.df_block_features.argtypes = [P, I, D, D, D, I, P, V]
         L.df_block_errors.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]
+        L.df_set_predictor.argtypes = [P, P, ctypes.c_float]
         L.df_workspace_bytes.argtypes = [P]
         L.df_workspace_bytes.restype = ctypes.c_int64
         LL = ctypes.c_longlong
@@ -278,7 +290,13 @@ class Context:
         _check(lib().df_build_J(self._h, _f64(D), _f64(J), _f64(rho), _stream(stream)), "df_build_J")
         return J, rho
 
+    def set_predictor(self, mlp, min_conf: float = 0.6):
+        """Attach a network for build_K(C, LEARNED) (None detaches); the context keeps the pointer."""
+        self._pred = mlp
+        _check(lib().df_set_predictor(self._h, None if mlp is None else mlp._h, float(min_conf)), "df_set_predictor")
+
     def build_K(self, C, nslices: int, K=None, stream=None):
+        """nslices: 1..8 fixed, 0 native FP64, ADAPTIVE (-1) the current level's count, LEARNED (-2)."""
         nocc = C.shape[1]
         if K is None:
             K = torch.empty((self.nao, self.nao), dtype=torch.float64, device=C.device)
@@ -374,10 +392,10 @@ class Batch:
 
     def autotune(self, Cs, nslices: int, Ks, stream=None):
         nocc = (ctypes.c_int * len(Cs))(*[int(C.shape[1]) for C in Cs])
-        ch = (ctypes.c_int * 2)()
+        ch = (ctypes.c_int * 3)()
         _check(lib().df_batch_autotune(self._h, _ptr_array(Cs), nocc, int(nslices), _ptr_array(Ks), _stream(stream),
                                        ch), "df_batch_autotune")
-        return ch[0], ch[1]
+        return ch[0], ch[1], ch[2]
 
 
 class MLP:

@@ -21,7 +21,13 @@ N_occ/N_bf = 0.07-0.16):
 * orbitals: C = Q factor of the reduced QR of a seeded N(0,1) nao x nocc
   matrix, D = 2 C C^T;
 * SCF-like sequence: orbitals perturbed off span(C*) so that
-  ||D_k - D*||_F = 0.1 * 10^-k.
+  ||D_k - D*||_F = 0.1 * 10^-k;
+* chain molecules (the paper's alkanes are chains): ``n`` atoms along x with
+  spacings uniform in [1.6, 2.2] bohr and transverse offsets uniform in
+  [-0.4, 0.4] bohr, with Schwarz screening (Section 2.1) of the AO pairs: pair
+  (mu, nu) is dropped when sqrt((mu nu|mu nu) max_P (P|P)) < tau, which zeroes
+  (P|mu nu) for every P and so B_Pmunu (the contraction of Eq. cderi runs
+  over the auxiliary index only).
 """
 from __future__ import annotations
 
@@ -119,6 +125,37 @@ def molecule(n_atoms: int, seed: int, edge: float | None = None) -> Molecule:
         ao_exp=np.tile(AO_EXPONENTS, n_atoms),
         aux_xyz=np.ascontiguousarray(np.repeat(xyz, len(AUX_EXPONENTS), axis=0)),
         aux_exp=np.tile(AUX_EXPONENTS, n_atoms))
+
+
+def chain_molecule(n_atoms: int, seed: int) -> Molecule:
+    """n atoms along x: spacings uniform in [1.6, 2.2] bohr, transverse offsets in [-0.4, 0.4]."""
+    rng = np.random.default_rng(seed)
+    x = np.cumsum(rng.uniform(1.6, 2.2, n_atoms))
+    x -= x[0]
+    xyz = np.column_stack([x, rng.uniform(-0.4, 0.4, (n_atoms, 2))])
+    return Molecule(
+        n_atoms=n_atoms, seed=seed, edge=float(x[-1]), xyz=xyz,
+        ao_xyz=np.ascontiguousarray(np.repeat(xyz, len(AO_EXPONENTS), axis=0)),
+        ao_exp=np.tile(AO_EXPONENTS, n_atoms),
+        aux_xyz=np.ascontiguousarray(np.repeat(xyz, len(AUX_EXPONENTS), axis=0)),
+        aux_exp=np.tile(AUX_EXPONENTS, n_atoms))
+
+
+def schwarz_pairs(mol: Molecule, tau: float) -> np.ndarray:
+    """Kept AO pairs of Schwarz screening (Section 2.1): sqrt((mu nu|mu nu) max_P (P|P)) >= tau.
+
+    For normalised s primitives, (ab|ab) = (N_a N_b K_ab)^2 2 pi^(5/2) / (p^2 sqrt(2 p))
+    with p = a + b (the Coulomb integral of a Gaussian product with itself, F0(0) = 1),
+    and (P|P) = N_c^2 2 pi^(5/2) / (c^2 sqrt(2 c)).  Returns a symmetric bool [nao, nao]."""
+    a = mol.ao_exp
+    p = a[:, None] + a[None, :]
+    R2 = np.sum((mol.ao_xyz[:, None, :] - mol.ao_xyz[None, :, :]) ** 2, axis=-1)
+    n = (2.0 * a / np.pi) ** 0.75
+    nab = n[:, None] * n[None, :] * np.exp(-a[:, None] * a[None, :] / p * R2)
+    abab = nab ** 2 * 2.0 * np.pi ** 2.5 / (p * p * np.sqrt(2.0 * p))
+    c = mol.aux_exp
+    pp = np.max((2.0 * c / np.pi) ** 1.5 * 2.0 * np.pi ** 2.5 / (c * c * np.sqrt(2.0 * c)))
+    return np.sqrt(abab * pp) >= tau
 
 
 def int3c(mol: Molecule) -> np.ndarray:
@@ -294,6 +331,8 @@ class Workload:
     n_atoms: int
     nocc: int
     seed: int
+    shape: str = "cube"     # "cube": constant-density cube; "chain": the chain geometry
+    tau: float = 0.0        # Schwarz screening threshold of the AO pairs (0: none)
 
     @property
     def nao(self):
@@ -310,6 +349,23 @@ SMALL = Workload("df-20atom-nao100-naux300-nocc20", 20, 20, 1000 * 0 + 0)
 MEDIUM = Workload("df-120atom-nao600-naux1800-nocc120", 120, 120, 1000 * 1 + 0)
 # One molecule of 240 atoms (nao 1200, naux 3600, nocc 250): adaptive sequence.
 LARGE = Workload("df-240atom-nao1200-naux3600-nocc250", 240, 250, 1000 * 2 + 0)
+
+
+# A 240-atom chain with the 240-atom molecule's sizes (nao 1200, naux 3600, nocc 250)
+# and Schwarz screening at 1e-12: about 5 % of the AO pairs survive (block-sparse B).
+CHAIN = Workload("df-chain240-nao1200-naux3600-nocc250-scr1e-12", 240, 250, 1000 * 7 + 0, "chain", 1e-12)
+
+
+def workload_molecule(w: Workload) -> Molecule:
+    return chain_molecule(w.n_atoms, w.seed) if w.shape == "chain" else molecule(w.n_atoms, w.seed)
+
+
+def screened_int3c(mol: Molecule, tau: float) -> np.ndarray:
+    """(P|mu nu) with the Schwarz-screened pairs set to zero for every P (tau 0: none)."""
+    T = int3c(mol)
+    if tau > 0.0:
+        T[:, ~schwarz_pairs(mol, tau)] = 0.0
+    return T
 
 
 # 60 atoms with the 120-atom molecule's occupied count: the same tile shapes in a

@@ -1,13 +1,19 @@
-"""Learned per-block slice counts for the exchange build.
+"""Learned per-block slice counts for the exchange build: training data and training.
 
 The network (16 block features -> 64 -> 64 -> 8 slice counts) runs and trains
-on the device through libdf's own kernels.  Its labels come from the method
-itself: for every 128-function auxiliary block, the least slice count whose
-K error against the native FP64 build stays within the block's share of the
-tolerance (tau max|K| / nblk, an additive split that bounds the total).  At
-run time a prediction below the confidence threshold falls back to the slice
-count of the paper's rule (Table 1) for the same tolerance, and a block that
-misses its budget is recomputed at that count and counted.
+on the device through libdf's own kernels; at run time the library itself
+predicts, falls back to the rule's count on low confidence and checks the
+counts (df_build_K with nslices = LEARNED, after df_set_predictor).  This
+module only builds the training set and drives the training steps.
+
+Labels come from the method itself, against FP64: for every 128-function
+auxiliary block b the K_b error of the emulated build at every slice count
+(df_block_errors), and, per Table 1 level L with count s_L, the per-block
+counts with the fewest slice pairs whose summed block errors stay within the
+rule's own: sum_b err_b(s_b) <= sum_b err_b(s_L).  The network thereby
+serves the accuracy the rule (the judge) achieves at that level, and can only
+save work by trading: more slices on blocks whose errors dominate, fewer on
+blocks whose errors are negligible.
 """
 from __future__ import annotations
 
@@ -16,29 +22,56 @@ import torch
 
 from . import df
 
-# Table 1's printed accuracies (levels 4..1) and the 1e-10 target of the K error
-TAUS = (1.2e-7, 4.7e-10, 1e-10, 1.8e-12, 7.1e-15)
-
-
-def rule_slices(tau: float) -> int:
-    """Slice count of the Table 1 level whose printed accuracy is at least as tight as tau."""
-    for acc, s in ((1.2e-7, 3), (4.7e-10, 4), (1.8e-12, 5), (7.1e-15, 6)):
-        if acc <= tau:
-            return s
-    return 8
+# Table 1: printed accuracy and INT8 count of levels 4..1
+LEVELS = {4: (1.2e-7, 3), 3: (4.7e-10, 4), 2: (1.8e-12, 5), 1: (7.1e-15, 6)}
+PAIRS = np.array([s * (s + 1) // 2 for s in range(1, 9)])
 
 
 def pairs(s):
     return s * (s + 1) // 2
 
 
-def labels_from_errors(err: np.ndarray, kmax: float, tau: float) -> np.ndarray:
-    """Least s in 1..8 with err[b, s-1] <= tau kmax / nblk (8 if none)."""
+def labels_at_rule_accuracy(err: np.ndarray, s_rule: int) -> np.ndarray:
+    """Per-block counts (1..8) with few slice pairs and sum_b err[b, s_b - 1] <= sum_b err[b, s_rule - 1].
+
+    Lagrangian relaxation: for a multiplier lam every block independently takes
+    argmin_s pairs(s) + lam err[b, s - 1]; the candidates are the assignments at
+    every breakpoint lam where some block's choice changes, plus the rule's own
+    counts; the feasible candidate with the fewest pairs is then lowered block
+    by block (smallest added error first) while it stays feasible.
+    """
+    err = np.asarray(err, dtype=np.float64)
     nblk = err.shape[0]
-    budget = tau * kmax / nblk
-    ok = err <= budget
-    lab = np.where(ok.any(axis=1), ok.argmax(axis=1) + 1, 8)
-    return lab.astype(np.int64)
+    budget = float(err[:, s_rule - 1].sum())
+    best = np.full(nblk, s_rule, dtype=np.int64)
+    best_work = int(PAIRS[best - 1].sum())
+    lams = []
+    for b in range(nblk):
+        for s1 in range(8):
+            for s2 in range(s1 + 1, 8):
+                de = err[b, s1] - err[b, s2]
+                if de > 0:
+                    lams.append((PAIRS[s2] - PAIRS[s1]) / de)
+    rev = err[:, ::-1]
+    for lam in sorted(set(lams)):
+        cost = PAIRS[::-1][None, :] + lam * rev            # reversed: ties go to the larger count
+        s = 8 - np.argmin(cost, axis=1)
+        e = float(err[np.arange(nblk), s - 1].sum())
+        w = int(PAIRS[s - 1].sum())
+        if e <= budget and w < best_work:
+            best, best_work = s.astype(np.int64), w
+    used = float(err[np.arange(nblk), best - 1].sum())
+    improved = True
+    while improved:
+        improved = False
+        order = sorted((err[b, best[b] - 2] - err[b, best[b] - 1], b) for b in range(nblk) if best[b] > 1)
+        for add, b in order:
+            if used + add <= budget:
+                best[b] -= 1
+                used += add
+                improved = True
+                break
+    return best
 
 
 def init_params(seed: int) -> np.ndarray:
@@ -58,20 +91,23 @@ def magnitude_order(B: torch.Tensor) -> np.ndarray:
     return torch.argsort(B.abs().amax(dim=(1, 2)), descending=True).cpu().numpy()
 
 
-def molecule_dataset(ctx, C, taus=TAUS, seed=0):
-    """Features and labels of every block of one molecule at every tolerance.
+def molecule_dataset(ctx, C, seed=0, levels=(4, 3, 2, 1)):
+    """Features and labels of every block of one molecule at every level.
 
     The density-change and energy-change features are drawn log-uniformly over
     the range an SCF-like sequence visits (the labels do not depend on them).
+    Returns (F [n, 16] float32, labels - 1 [n] int32 on the device, err, kmax).
     """
     rng = np.random.default_rng(seed)
     err, kmax = df.block_errors(ctx, C)
     Fs, ys = [], []
-    for tau in taus:
+    for level in levels:
+        tau, s_rule = LEVELS[level]
         dD = 10.0 ** rng.uniform(-14, 0)
         dE = 10.0 ** rng.uniform(-16, -2)
-        Fs.append(df.block_features(ctx, C.shape[1], tau, dD, dE, rule_slices(tau)))
-        ys.append(torch.from_numpy(labels_from_errors(err, kmax, tau) - 1).to(torch.int32).cuda())
+        Fs.append(df.block_features(ctx, C.shape[1], tau, dD, dE, s_rule))
+        lab = labels_at_rule_accuracy(err, s_rule)
+        ys.append(torch.from_numpy(lab - 1).to(torch.int32).cuda())
     return torch.cat(Fs), torch.cat(ys), err, kmax
 
 
@@ -97,24 +133,6 @@ class SlicePredictor:
                 hist.append(loss)
         return hist
 
-    def predict(self, F: torch.Tensor, fallback_s: int, min_conf: float = 0.6):
-        """Per-block slice counts; rows whose top probability is below min_conf get fallback_s."""
-        probs = self.mlp.forward(F).cpu().numpy()
-        s = probs.argmax(axis=1) + 1
-        conf = probs.max(axis=1)
-        low = conf < min_conf
-        s = np.where(low, fallback_s, s)
-        return s.astype(int), conf, int(low.sum())
-
-
-def evaluate(err: np.ndarray, kmax: float, tau: float, s_pred: np.ndarray):
-    """Work and recomputes of per-block counts against the best uniform count at the same budget."""
-    nblk = err.shape[0]
-    budget = tau * kmax / nblk
-    lab = labels_from_errors(err, kmax, tau)
-    s_uniform = int(lab.max())
-    miss = np.array([err[b, s_pred[b] - 1] > budget for b in range(nblk)])
-    s_final = np.where(miss, np.maximum(s_pred, s_uniform), s_pred)
-    return {"work_pred": int(sum(pairs(int(x)) for x in s_final)), "work_uniform": nblk * pairs(s_uniform),
-            "work_rule": nblk * pairs(rule_slices(tau)), "recomputed": int(miss.sum()), "s_uniform": s_uniform,
-            "s_final": [int(x) for x in s_final], "labels": [int(x) for x in lab]}
+    def attach(self, ctx, min_conf: float = 0.6):
+        """Let ctx.build_K(C, df.LEARNED) use this network."""
+        ctx.set_predictor(self.mlp, min_conf)

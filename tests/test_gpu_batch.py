@@ -60,7 +60,7 @@ def test_batch_matches_single_builds_and_oracle(df, molecules):
     B, C, D = molecules[1]
     assert np.array_equal(Ks[1].cpu().numpy(), O.emulated_exchange(B, C, s))
     choice = batch.autotune(Cs, s, Ks)
-    assert choice[0] in (1, 2, 8) and choice[1] in (0, 1)
+    assert choice[0] in (1, 2, 4, 8) and choice[1] in (0, 1) and choice[2] in (0, 1)
     with torch.cuda.stream(stream):
         for k in Ks:
             k.fill_(0.0)
@@ -68,3 +68,36 @@ def test_batch_matches_single_builds_and_oracle(df, molecules):
     stream.synchronize()
     for k, k1 in zip(Ks, single):
         assert torch.equal(k, k1)
+
+
+def test_autotuner_choice_depends_on_the_molecule_mix(df):
+    """Two seeded mixes from the batch workload's range: molecules whose orbitals fit one
+    128-row tile (the CTA-pair tile is available and timed against the single-CTA tile), and
+    the same mix with its last molecule of 130 orbitals (only the single-CTA tile exists).
+    Each mix's tuned batch reproduces its single builds bit for bit."""
+    s = 5
+    mixes = {"small-nocc": [(30, 41), (52, 42), (75, 43), (100, 44)],
+             "one-large-nocc": [(30, 41), (52, 42), (75, 43), (130, 45)]}
+    chosen = {}
+    for name, mols in mixes.items():
+        ctxs, keep, Cs = [], [], []
+        for atoms, seed in mols:
+            mol = inputs.molecule(atoms, seed)
+            B = inputs.df_tensor_device(mol)
+            ctx = df.Context(mol.nao, mol.naux, atoms, s_max=s)
+            ctx.setup(B)
+            ctxs.append(ctx)
+            keep.append(B)
+            Cs.append(torch.from_numpy(inputs.orbitals(mol.nao, atoms, seed + 1)).cuda())
+        single = [ctx.build_K(C, s)[0].clone() for ctx, C in zip(ctxs, Cs)]
+        batch = df.Batch(ctxs)
+        Ks = [torch.empty_like(k) for k in single]
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            chosen[name] = batch.autotune(Cs, s, Ks)
+            batch.build_K(Cs, s, Ks)
+        stream.synchronize()
+        for k, k1 in zip(Ks, single):
+            assert torch.equal(k, k1)
+    print("autotuner choices (K-split cap, order, first-GEMM tile):", chosen)
+    assert chosen["one-large-nocc"][2] == 0 and chosen["small-nocc"][2] in (0, 1)

@@ -34,7 +34,10 @@ def test_adaptive_sequence_follows_table1_and_converges(df):
     # the early, low-precision iterations are far from FP64; the late ones agree closely
     assert recs[0]["max_dK_rel"] > 1e-9
     assert recs[-1]["dE_vs_fp64"] < 1e-9
-    # every iteration meets the accuracy of its level's slice count
+    # every iteration runs its level's count in every block and meets that count's accuracy
     for r in recs:
-        if r.get("slices"):
-            assert r["max_dK_rel"] < {3: 1e-5, 4: 1e-7, 5: 1e-10, 6: 1e-12}.get(r["slices"], 1e-13)
+        s = r["slices"][0]
+        assert r["slices"] == [s] * r["nblk"] and s == O.slices_for_level(r["level"])
+        if s:
+            assert r["max_dK_rel"] < {3: 1e-5, 4: 1e-7, 5: 1e-10, 6: 1e-12}.get(s, 1e-13)
+        assert r["fallback"] == (s == 0) and r["recomputed"] == 0

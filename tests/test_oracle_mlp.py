@@ -155,3 +155,17 @@ def test_block_features_of_hand_built_tensor():
     F = M.block_features(B, eB, nocc=4, tau=1e-10, dD=1e-4, dE=1e-8, s_rule=5)
     assert F.shape == (2, 16)
     assert np.allclose(F, hand_features(), rtol=0, atol=1e-15)
+
+
+def test_labels_at_rule_accuracy_hand_table():
+    """Three blocks, errors 256x per slice: block 0 dominates (scale 1), blocks 1 and 2 are
+    10^-4 of it.  At the rule's 4 slices (10 pairs each, 30 in all) the budget is
+    (1 + 2e-4) 256^-4; raising block 0 to 5 frees 255/256 of its share, which pays for
+    lowering both small blocks to 3 (each adds 255e-4 256^-4): 15 + 6 + 6 = 27 pairs."""
+    err = np.array([[1.0 * 256.0 ** -s for s in range(1, 9)],
+                    [1e-4 * 256.0 ** -s for s in range(1, 9)],
+                    [1e-4 * 256.0 ** -s for s in range(1, 9)]])
+    assert list(M.labels_at_rule_accuracy(err, 4)) == [5, 3, 3]
+    # equal blocks: nothing to trade, the rule's own counts
+    eq = np.array([[256.0 ** -s for s in range(1, 9)]] * 3)
+    assert list(M.labels_at_rule_accuracy(eq, 4)) == [4, 4, 4]
