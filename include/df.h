@@ -75,7 +75,11 @@ void df_destroy(df_ctx *ctx);
 /* Attach the DF tensor B (Eq. cderi; device, [naux][nao][nao], caller-owned
  * and kept alive for the context's lifetime) and split it once into s_max
  * INT8 digit planes with one power-of-two exponent per (P, mu) row
- * (Section 3.2).  B is constant over the SCF iterations, so this runs once. */
+ * (Section 3.2).  B is constant over the SCF iterations, so this runs once.
+ * Every B_P must be exactly symmetric (B_P mu nu == B_P nu mu bit for bit, as
+ * Eq. cderi gives it in exact arithmetic; rho and J read only the upper
+ * triangle): the call checks this on the device and returns DF_ERR_ARG
+ * otherwise (also for a NaN).  Synchronises `stream`. */
 df_status df_setup(df_ctx *ctx, const double *B_dev, void *stream);
 
 /* As df_setup, with the exchange path taking the auxiliary functions in the
@@ -319,7 +323,9 @@ df_status df_block_features(df_ctx *ctx, int nocc, double tau, double dD, double
  * df_build_J calls, the last relative energy change seen by
  * df_adaptive_next, and s_L), runs the network, and takes for block b the
  * most probable count s_b, or s_L when that probability is below min_conf
- * (in (0, 1]).  After the first GEMM and the X split it checks, without any
+ * (in (0, 1]); a count above s_L only pays for another block below s_L, so
+ * when no block is below s_L every block takes s_L.  After the first GEMM
+ * and the X split it checks, without any
  * FP64 reference, the a-priori error bound of every block's K_b
  *   beta_b(s) = kb_b 1.01 (s + 1) 2^(-8 s) (2^(2 E_b) + 2 nao 2^(F_b + E_c + E_b))
  *               + kb_b 2^(2 E_b - 52)
@@ -360,6 +366,19 @@ df_status df_phase_times(df_ctx *ctx, double *ms, int *count);
 /* Device bytes held by the context's workspaces. */
 int64_t df_workspace_bytes(const df_ctx *ctx);
 
+/* Block sparsity found by df_setup (the Schwarz screening of Section 2.1
+ * zeroes a screened AO pair (mu, nu) in every B_P; the paper's FLOP model
+ * counts the surviving pairs as N_scr).  At setup the library records, per mu,
+ * which 64-wide chunks of nu hold a nonzero B_P mu nu for some P; when some
+ * chunk is zero (and nao <= 2048) the first exchange GEMM runs only the
+ * nonzero 64-wide K tiles of each 128-row tile of B's (P, mu) rows, and rho
+ * and J skip the zero chunks.  Skipped terms are exact zeros: every result is
+ * the one of the dense build.  frac_ktiles: nonzero K tiles / all of the first
+ * GEMM's row tiles; frac_chunks: nonzero (mu, chunk) pairs of the upper
+ * triangle / all.  Both 1 for a B without zero chunks.  DF_ERR_STATE before
+ * setup. */
+df_status df_sparsity(const df_ctx *ctx, double *frac_ktiles, double *frac_chunks);
+
 /* Execution options of a context (they change speed, never results: every
  * option gives bit-identical K).
  *
@@ -375,6 +394,9 @@ int64_t df_workspace_bytes(const df_ctx *ctx);
  *
  * Returns DF_ERR_ARG for an unknown option or value; the context is unchanged. */
 #define DF_OPT_CLUSTER_PAIRS 1
+/* DF_OPT_SPARSE — whether the builds use the block sparsity of a screened B
+ * (df_sparsity): 1 (default) when df_setup found zero chunks, 0 never. */
+#define DF_OPT_SPARSE 2
 df_status df_set_option(df_ctx *ctx, int option, int value);
 
 #ifdef __cplusplus

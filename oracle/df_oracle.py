@@ -105,6 +105,23 @@ def eri4(ao_xyz, ao_exp):
                        p[None, None, :, :], Pc[None, None, :, :, :])).reshape(n, n, n, n)
 
 
+def pair_self_coulomb(ao_xyz, ao_exp):
+    """(ab|ab) for every AO pair: the Coulomb self-interaction of the normalised
+    Gaussian product a*b (Gaussian product theorem, then the s-type Coulomb
+    integral at zero separation)."""
+    a = ao_exp
+    p, Pc, Kab = gaussian_product(a[:, None], ao_xyz[:, None, :], a[None, :], ao_xyz[None, :, :])
+    nab = norm_s(a)[:, None] * norm_s(a)[None, :] * Kab
+    return nab * nab * coulomb_ss(p, Pc, p, Pc)
+
+
+def schwarz_keep(ao_xyz, ao_exp, aux_xyz, aux_exp, tau):
+    """Schwarz screening of Section 2.1: keep the pair (a, b) unless
+    sqrt((ab|ab) max_P (P|P)) < tau.  Returns a bool [nao, nao]."""
+    pp = float(np.max(np.diag(metric(aux_xyz, aux_exp))))
+    return np.sqrt(pair_self_coulomb(ao_xyz, ao_exp) * pp) >= tau
+
+
 # ---------------------------------------------------------------------------
 # DF tensor, Section 2.1 Eq. cderi
 # ---------------------------------------------------------------------------

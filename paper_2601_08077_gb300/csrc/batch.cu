@@ -247,8 +247,9 @@ df_status df_batch_build_J(df_batch *b, const double *const *D, double *const *J
     for (int i = 0; i < n; ++i) {
       df_ctx *c = b->ctx[i];
       if (!c->ready) return DF_ERR_STATE;
-      if (df::launch_rho(c->B, D[i], c->naux, c->nao, c->rho, st) != cudaSuccess) return DF_ERR_CUDA;
-      if (df::launch_coulomb(c->B, c->rho, c->naux, c->nao, J[i], st) != cudaSuccess) return DF_ERR_CUDA;
+      const uint32_t *mk = df::use_mask_mu(c);
+      if (df::launch_rho(c->B, D[i], c->naux, c->nao, c->rho, st, mk) != cudaSuccess) return DF_ERR_CUDA;
+      if (df::launch_coulomb(c->B, c->rho, c->naux, c->nao, J[i], st, mk) != cudaSuccess) return DF_ERR_CUDA;
     }
     return DF_OK;
   };

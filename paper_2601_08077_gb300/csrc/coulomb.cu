@@ -11,6 +11,11 @@
 // (Section 3.1).  On GB300 the FP64 pipe is narrow, so these kernels are
 // bounded by FP64 FMA throughput rather than by HBM; the roofline reported
 // for them uses the measured FP64 rate.
+//
+// A Schwarz-screened B (Section 2.1: a screened AO pair is zero in every B_P)
+// is block-sparse: with per-mu masks of the 64-wide nu chunks that hold a
+// nonzero, both passes skip the zero chunks (rho loses only zero terms; J is
+// exactly zero there), cutting bytes and FMAs to the surviving pairs.
 #include "df_internal.h"
 
 namespace df {
@@ -23,9 +28,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One CTA per P.  Warp w takes rows mu = w, w + 8, ...; lanes stride nu >= mu.
+// One CTA per P.  Warp w takes rows mu = w, w + 8, ...; lanes stride nu >= mu
+// (with masks: over the nonzero 64-wide chunks of the row only).
 __global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, const double *__restrict__ D,
-                                                  int nao, double *__restrict__ rho) {
+                                                  int nao, double *__restrict__ rho,
+                                                  const uint32_t *__restrict__ mask_mu) {
   const int P = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double *BP = B + (long long)P * nao * nao;
@@ -34,7 +41,16 @@ __global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, 
     const double *brow = BP + (long long)mu * nao;
     const double *drow = D + (long long)mu * nao;
     if (lane == 0) dia = fma(__ldg(brow + mu), __ldg(drow + mu), dia);
-    for (int nu = mu + 1 + lane; nu < nao; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+    if (mask_mu) {
+      const uint32_t mk = __ldg(mask_mu + mu);
+      for (int c = (mu + 1) >> 6; c * 64 < nao; ++c) {
+        if (!((mk >> c) & 1u)) continue;
+        const int hi = min(nao, c * 64 + 64);
+        for (int nu = max(mu + 1, c * 64) + lane; nu < hi; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+      }
+    } else {
+      for (int nu = mu + 1 + lane; nu < nao; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+    }
   }
   double v = 2.0 * off + dia;
   v = warp_sum(v);
@@ -54,7 +70,8 @@ __global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, 
 // row alone in the middle when nao is odd), so every CTA has the same work.
 // Each element's sum runs over P in ascending order, one FMA per P.
 __global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__ B, const double *__restrict__ rho,
-                                                      int naux, int nao, double *__restrict__ J) {
+                                                      int naux, int nao, double *__restrict__ J,
+                                                      const uint32_t *__restrict__ mask_mu) {
   extern __shared__ double srho[];
   for (int i = threadIdx.x; i < naux; i += blockDim.x) srho[i] = rho[i];
   __syncthreads();
@@ -66,6 +83,12 @@ __global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__
   const int nu = e < len0 ? m0 + e : m1 + (e - len0);
   const long long off = (long long)mu * nao + nu;
   const long long stride = (long long)nao * nao;
+  if (mask_mu && !((__ldg(mask_mu + mu) >> (nu >> 6)) & 1u)) {
+    // a screened pair: B_P mu nu = 0 for every P
+    J[off] = 0.0;
+    J[(long long)nu * nao + mu] = 0.0;
+    return;
+  }
   double acc = 0.0;
   int P = 0;
   for (; P + 4 <= naux; P += 4) {
@@ -164,9 +187,90 @@ __global__ void density_change_final_kernel(const double *__restrict__ part, int
   }
 }
 
+// Sets *flag when some B_P is not exactly symmetric (a NaN counts as
+// asymmetric).  Block (x, y, P) with x <= y compares the 32 x 32 tile (x, y) of
+// B_P, staged in shared memory, with the transpose of tile (y, x).
+__global__ void __launch_bounds__(256) symmetry_check_kernel(const double *__restrict__ B, int nao,
+                                                             int *__restrict__ flag) {
+  const int bi = blockIdx.x, bj = blockIdx.y;
+  if (bi > bj) return;
+  __shared__ double t[32][33];
+  const double *BP = B + (long long)blockIdx.z * nao * nao;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi * 32 + r, j = bj * 32 + tx;
+    if (i < nao && j < nao) t[r][tx] = BP[(long long)i * nao + j];
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bj * 32 + r, j = bi * 32 + tx;  // B[i][j] must equal B[j][i] = t[tx][r]
+    if (i < nao && j < nao && !(BP[(long long)i * nao + j] == t[tx][r])) bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && tx == 0) atomicOr(flag, 1);
+}
+
+// Per mu: bit c set when some B_P mu nu, nu in [64c, 64c + 64), is nonzero.
+// One CTA per mu, over every P (one pass over B at setup).
+__global__ void __launch_bounds__(256) pair_mask_kernel(const double *__restrict__ B, int naux, int nao,
+                                                        uint32_t *__restrict__ mask_mu) {
+  const int mu = blockIdx.x;
+  uint32_t bits = 0u;
+  const long long n2 = (long long)nao * nao;
+  for (int P = 0; P < naux; ++P) {
+    const double *row = B + (long long)P * n2 + (long long)mu * nao;
+    for (int nu = threadIdx.x; nu < nao; nu += blockDim.x)
+      if (__ldg(row + nu) != 0.0) bits |= 1u << (nu >> 6);
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  __shared__ uint32_t red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bits;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) bits |= red[w];
+    mask_mu[mu] = bits;
+  }
+}
+
+// Per 128-row tile t of the (P, mu) rows (row r has mu = r mod nao): the OR of
+// its rows' masks.
+__global__ void tile_mask_kernel(const uint32_t *__restrict__ mask_mu, int nao, long long rows, int ntiles,
+                                 uint32_t *__restrict__ mask_tile) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  uint32_t m = 0u;
+  const long long r0 = (long long)t * kTile;
+  for (long long r = r0; r < r0 + kTile && r < rows; ++r) m |= mask_mu[r % nao];
+  mask_tile[t] = m;
+}
+
 }  // namespace
 
 constexpr int kEnergyBlocks = 296;
+
+cudaError_t launch_symmetry_check(const double *B, int naux, int nao, int *flag, cudaStream_t st) {
+  const int nt = (nao + 31) / 32;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  for (int p0 = 0; p0 < naux; p0 += 65535) {
+    const int np = naux - p0 < 65535 ? naux - p0 : 65535;
+    symmetry_check_kernel<<<dim3(nt, nt, np), 256, 0, st>>>(B + (long long)p0 * nao * nao, nao, flag);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_pair_masks(const double *B, int naux, int nao, uint32_t *mask_mu, uint32_t *mask_tile,
+                              cudaStream_t st) {
+  pair_mask_kernel<<<nao, 256, 0, st>>>(B, naux, nao, mask_mu);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long rows = (long long)naux * nao;
+  const int ntiles = (int)((rows + kTile - 1) / kTile);
+  tile_mask_kernel<<<(ntiles + 255) / 256, 256, 0, st>>>(mask_mu, nao, rows, ntiles, mask_tile);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_density_change(const double *D, double *Dprev, bool have_prev, long long n2, double *part,
                                   double *out, cudaStream_t st) {
@@ -179,12 +283,14 @@ cudaError_t launch_density_change(const double *D, double *Dprev, bool have_prev
   return cudaMemcpyAsync(Dprev, D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, st);
 }
 
-cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st) {
-  rho_kernel<<<naux, 256, 0, st>>>(B, D, nao, rho);
+cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st,
+                       const uint32_t *mask_mu) {
+  rho_kernel<<<naux, 256, 0, st>>>(B, D, nao, rho, mask_mu);
   return cudaGetLastError();
 }
 
-cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st) {
+cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st,
+                           const uint32_t *mask_mu) {
   const size_t sm = (size_t)naux * sizeof(double);
   static size_t attr = 48 * 1024;
   if (sm > attr) {
@@ -193,7 +299,7 @@ cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao
     attr = sm;
   }
   dim3 grid((nao + 1 + 255) / 256, (nao + 1) / 2);
-  coulomb_kernel<<<grid, 256, sm, st>>>(B, rho, naux, nao, J);
+  coulomb_kernel<<<grid, 256, sm, st>>>(B, rho, naux, nao, J, mask_mu);
   return cudaGetLastError();
 }
 

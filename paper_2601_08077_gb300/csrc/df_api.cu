@@ -169,6 +169,7 @@ bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap 
     p.out_ld = nocc;
     p.status = c->status;
     p.pair = c->pair_mode;
+    p.kmask = use_mask_tile(c);
     return true;
   }
   if (!make_tmap_bf16(&ta, c->Cd, nao, nocc, c->s_max, c->ld_nao, c_plane)) return false;
@@ -195,6 +196,7 @@ bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap 
   p.out_ld = nocc;
   p.status = c->status;
   p.pair = c->pair_mode;
+  p.kmask = use_mask_tile(c);
   return true;
 }
 
@@ -453,6 +455,8 @@ void df_destroy(df_ctx *c) {
   cudaFree(c->lexp);
   if (c->lhost) cudaFreeHost(c->lhost);
   cudaFree(c->bstats);
+  cudaFree(c->mask_mu);
+  cudaFree(c->mask_tile);
   cudaFree(c->perm);
   if (c->sblk_host) cudaFreeHost(c->sblk_host);
   for (int ph = 0; ph < DF_NPHASES; ++ph)
@@ -468,6 +472,14 @@ void df_destroy(df_ctx *c) {
 
 int64_t df_workspace_bytes(const df_ctx *c) { return c ? c->bytes : 0; }
 
+df_status df_sparsity(const df_ctx *c, double *frac_ktiles, double *frac_chunks) {
+  if (!c || !frac_ktiles || !frac_chunks) return DF_ERR_ARG;
+  if (!c->ready) return DF_ERR_STATE;
+  *frac_ktiles = c->frac_ktiles;
+  *frac_chunks = c->frac_chunks;
+  return DF_OK;
+}
+
 df_status df_set_profiling(df_ctx *c, int on) {
   if (!c) return DF_ERR_ARG;
   c->profiling = on != 0;
@@ -480,6 +492,10 @@ df_status df_set_option(df_ctx *c, int option, int value) {
     case DF_OPT_CLUSTER_PAIRS:
       if (value < 0 || value > 2) return DF_ERR_ARG;
       c->pair_mode = value;
+      return DF_OK;
+    case DF_OPT_SPARSE:
+      if (value < 0 || value > 1) return DF_ERR_ARG;
+      c->sparse_opt = value;
       return DF_OK;
   }
   return DF_ERR_ARG;
@@ -531,9 +547,43 @@ df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host,
     cudaFree(c->bstats);
     c->bstats = nullptr;
   }
+  c->ready = false;
+  // rho and J read the upper triangle of each B_P: B_P must be exactly symmetric
+  {
+    int h = 0;
+    DF_TRY(c, df::launch_symmetry_check(B_dev, c->naux, c->nao, c->status, st));
+    DF_TRY(c, cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DF_TRY(c, cudaStreamSynchronize(st));
+    DF_TRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), st));
+    if (h) return record(c, DF_ERR_ARG);
+  }
   const long long rows = (long long)c->naux * c->nao;
   DF_TRY(c, df::launch_split_rows_bf16(B_dev, rows, c->nao, c->nao, c->s_max, c->eB, c->Bd, c->ld_nao,
                                        rows * c->ld_nao, st, c->perm, c->nao));
+  // block sparsity of a screened B (Section 2.1): exact zero chunks of the AO pairs
+  c->sparse = false;
+  c->frac_ktiles = c->frac_chunks = 1.0;
+  if (c->nao <= 32 * df::kKTile) {
+    const int ntiles = (int)((rows + df::kTile - 1) / df::kTile);
+    if (!c->mask_mu) DF_TRY(c, cudaMalloc(&c->mask_mu, sizeof(uint32_t) * c->nao));
+    if (!c->mask_tile) DF_TRY(c, cudaMalloc(&c->mask_tile, sizeof(uint32_t) * ntiles));
+    DF_TRY(c, df::launch_pair_masks(B_dev, c->naux, c->nao, c->mask_mu, c->mask_tile, st));
+    std::vector<uint32_t> mu(c->nao), tiles(ntiles);
+    DF_TRY(c, cudaMemcpyAsync(mu.data(), c->mask_mu, sizeof(uint32_t) * c->nao, cudaMemcpyDeviceToHost, st));
+    DF_TRY(c, cudaMemcpyAsync(tiles.data(), c->mask_tile, sizeof(uint32_t) * ntiles, cudaMemcpyDeviceToHost, st));
+    DF_TRY(c, cudaStreamSynchronize(st));
+    const int nk = (c->nao + df::kKTile - 1) / df::kKTile;
+    long long on = 0, all = 0, kon = 0;
+    for (int m = 0; m < c->nao; ++m)
+      for (int k = m / df::kKTile; k < nk; ++k) {
+        ++all;
+        on += (mu[m] >> k) & 1u;
+      }
+    for (uint32_t t : tiles) kon += __builtin_popcount(t);
+    c->frac_chunks = all ? (double)on / all : 1.0;
+    c->frac_ktiles = (double)kon / ((double)ntiles * nk);
+    c->sparse = on < all;
+  }
   c->ready = true;
   return DF_OK;
 }
@@ -545,11 +595,11 @@ df_status df_build_J(df_ctx *c, const double *D, double *J, double *rho, void *s
   double *r = rho ? rho : c->rho;
   {
     PhaseTimer t(c, DF_PHASE_RHO, st);
-    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, r, st));
+    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, r, st, df::use_mask_mu(c)));
   }
   {
     PhaseTimer t(c, DF_PHASE_COULOMB, st);
-    DF_TRY(c, df::launch_coulomb(c->B, r, c->naux, c->nao, J, st));
+    DF_TRY(c, df::launch_coulomb(c->B, r, c->naux, c->nao, J, st, df::use_mask_mu(c)));
   }
   if (rho && rho != c->rho)
     DF_TRY(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * c->naux, cudaMemcpyDeviceToDevice, st));

@@ -27,6 +27,15 @@ struct df_ctx {
   int *sblk_host = nullptr; // pinned mirror of the last upload
   int *status = nullptr;
   double *bstats = nullptr;  // static per-block statistics for the predictor's features
+  // block sparsity of a screened B (set up by df_setup): per mu the mask of
+  // nonzero 64-wide nu chunks, per 128-row tile of (P, mu) rows the OR of its
+  // rows' masks; used only when some chunk is zero (sparse)
+  uint32_t *mask_mu = nullptr;
+  uint32_t *mask_tile = nullptr;
+  bool sparse = false;
+  int sparse_opt = 1;        // DF_OPT_SPARSE: 0 never use the masks, 1 when some chunk is zero
+  double frac_ktiles = 1.0;  // nonzero K tiles of the first GEMM's row tiles
+  double frac_chunks = 1.0;  // nonzero (mu, 64-wide nu chunk) pairs of the upper triangle
   int *perm = nullptr;       // exchange-path order of the auxiliary functions (P' -> P), or null
   std::vector<int> perm_h;   // host copy of perm (empty: natural order)
   int64_t bytes = 0;
@@ -70,6 +79,9 @@ df_status ctx_upload_slices(df_ctx *c, const int *sb, cudaStream_t st);
 bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap &tb, int swap = 1);
 bool gemm2_setup(df_ctx *c, int nocc, int nsplit, SgParams &q2, CUtensorMap &tx);
 long long xdigit_ld(int nocc);
+// The sparsity masks to use (null: run dense).
+inline const uint32_t *use_mask_mu(const df_ctx *c) { return c->sparse && c->sparse_opt ? c->mask_mu : nullptr; }
+inline const uint32_t *use_mask_tile(const df_ctx *c) { return c->sparse && c->sparse_opt ? c->mask_tile : nullptr; }
 // The two halves of an emulated exchange build with per-block counts sb:
 // the front uploads sb, splits C into c_planes digit planes (>= max sb), runs
 // the first GEMM and the X split; the back runs the second GEMM and the

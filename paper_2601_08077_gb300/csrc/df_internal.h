@@ -73,6 +73,10 @@ struct SgParams {
   int pair;
   int npairs;
   int crt_mod[kCrtMaxModuli];  // kModeMod: the modulus of each plane
+  // first exchange GEMM on a screened (block-sparse) B: per 128-row tile of
+  // B's (P, mu) rows, the bit mask of its nonzero 64-wide K tiles (bit k = K
+  // tile k, at most 32); null = dense
+  const uint32_t *kmask;
 };
 
 // Tile pairs of a launch in CTA-pair mode (0 = the layout has no pairing):
@@ -150,8 +154,19 @@ int slice_gemm_grid(int nunits);
 cudaError_t launch_wait_selftest(int *status, unsigned long long limit_ns, cudaStream_t st);
 int fixed_point_shift(int s, long long k);
 
-cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st);
-cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st);
+// mask_mu (optional, block-sparse B): per mu, bit c set when some B_P mu nu
+// with nu in [64c, 64c + 64) is nonzero; null = dense.
+cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st,
+                       const uint32_t *mask_mu = nullptr);
+cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st,
+                           const uint32_t *mask_mu = nullptr);
+// Sets *flag (zeroed first) when some B_P of B [naux][nao][nao] is not exactly
+// symmetric.
+cudaError_t launch_symmetry_check(const double *B, int naux, int nao, int *flag, cudaStream_t st);
+// The masks of a screened B: mask_mu as above (nao <= 2048) and, per
+// 128-row tile of the (P, mu) rows, the OR of its rows' mu masks.
+cudaError_t launch_pair_masks(const double *B, int naux, int nao, uint32_t *mask_mu, uint32_t *mask_tile,
+                              cudaStream_t st);
 cudaError_t launch_energy(const double *D, const double *J, const double *K, const double *rho, int nao,
                           int naux, double *partials, double *E_dev, cudaStream_t st);
 

@@ -599,6 +599,12 @@ df_status build_K_learned(df_ctx *c, const double *C, int nocc, double *K, df_ks
   std::vector<int> sb(c->lhost, c->lhost + nblk);
   int low = 0;
   for (int b = 0; b < nblk; ++b) low += c->lhost[nblk + b];
+  // a count above the level's only pays for another below it: with none below,
+  // every block takes the level's count
+  bool below = false;
+  for (int b = 0; b < nblk; ++b) below = below || sb[b] < s_rule;
+  if (!below)
+    for (int b = 0; b < nblk; ++b) sb[b] = std::min(sb[b], s_rule);
   // 2. first GEMM and X split at the predicted counts (C split deep enough for s_rule)
   df_status r = k_front(c, C, nocc, sb.data(), s_rule, st);
   if (r != DF_OK) return r;

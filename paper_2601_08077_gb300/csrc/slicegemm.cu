@@ -96,7 +96,17 @@ constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)
 
 struct Unit {
   int m0, n0, az0, azs, bz0, bzs, kt0, ktiles, s, blk, part;
+  // block-sparse K (first exchange GEMM on a screened B): the unit's nonzero
+  // K tiles as a bit mask; ktiles then counts its set bits
+  int sparse;
+  uint32_t kmask;
 };
+
+// Index of the unit's i-th K tile: the i-th set bit of the mask when the
+// unit is block-sparse, else kt0 + i.
+__device__ __forceinline__ int ktile_of(const Unit &w, int i) {
+  return w.sparse ? (int)__fns(w.kmask, 0u, i + 1) : w.kt0 + i;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -292,6 +302,8 @@ __device__ __forceinline__ Unit kpart_unit(const SgParams &p, int i, int j, int 
   w.s = p.s_blk[b];
   w.blk = b;
   w.part = bs;
+  w.sparse = 0;
+  w.kmask = 0u;
   return w;
 }
 
@@ -307,6 +319,16 @@ __device__ __forceinline__ Unit grid_unit(const SgParams &p, int mt, int nt) {
   w.kt0 = 0;
   w.part = 0;
   w.ktiles = p.ktiles;
+  w.sparse = 0;
+  w.kmask = 0u;
+  if (p.kmask && (p.layout == kLayoutX || p.layout == kLayoutXs)) {
+    // the (P, mu) row tile of B's digits: the n tile (kLayoutX) or the m tile (kLayoutXs)
+    const int t = p.layout == kLayoutX ? nt : mt;
+    const int ntile = p.layout == kLayoutX ? p.nt_n : p.nt_m;
+    w.sparse = 1;
+    w.kmask = t < ntile ? p.kmask[t] : 0u;
+    w.ktiles = __popc(w.kmask);
+  }
   if (p.layout == kLayoutX || p.layout == kLayoutXs) {
     // the (P, mu) rows of a 128-function block: a tile never straddles two blocks
     const long long r0 = p.layout == kLayoutX ? (long long)w.n0 : (long long)w.m0;
@@ -368,8 +390,15 @@ __device__ __forceinline__ Unit decode_pair(const SgParams &p, int pu, int r) {
   if (p.layout == kLayoutXs) {
     // (P, mu) tiles 2a, 2a+1 (the second may lie past the last: zeros, no
     // stores); the orbital tiles of one pair of (P, mu) tiles run back to
-    // back, so its B-digit tiles are reused from L2
-    return grid_unit(p, 2 * (pu / p.nt_n) + r, pu % p.nt_n);
+    // back, so its B-digit tiles are reused from L2.  Block-sparse: both CTAs
+    // run the union of the two tiles' K tiles (one MMA covers both).
+    Unit w = grid_unit(p, 2 * (pu / p.nt_n) + r, pu % p.nt_n);
+    if (w.sparse) {
+      const int other = 2 * (pu / p.nt_n) + (1 - r);
+      if (other < p.nt_m) w.kmask |= p.kmask[other];
+      w.ktiles = __popc(w.kmask);
+    }
+    return w;
   }
   const int h = p.nt_m >> 1;
   return grid_unit(p, 2 * (pu % h) + r, pu / h);
@@ -590,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 uint8_t *sa = smem + stage * SB;
                 uint8_t *sb = sa + kTileBytes;
-                const int kc = (w.kt0 + kt) * kKTile;
+                const int kc = ktile_of(w, kt) * kKTile;
                 if (kPair) {
                   // rank r holds B_{u0+r}; a single pair leaves rank 1's B
                   // rows unloaded (their MMA columns 128-255 are not read).

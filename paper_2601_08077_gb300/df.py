@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdf.so")
 S_MAX = 8
 AUX_BLOCK = 128
 OPT_CLUSTER_PAIRS = 1  # DF_OPT_CLUSTER_PAIRS
+OPT_SPARSE = 2         # DF_OPT_SPARSE
 PHASES = ("split_C", "gemm1", "split_X", "gemm2", "reduce", "rho", "coulomb", "energy")
 
 _STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA or cuBLAS call failed", -3: "device allocation failed",
@@ -108,6 +109,7 @@ def lib():
         L.df_block_features.argtypes = [P, I, D, D, D, I, P, V]
         L.df_block_errors.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]
         L.df_set_predictor.argtypes = [P, P, ctypes.c_float]
+        L.df_sparsity.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.df_workspace_bytes.argtypes = [P]
         L.df_workspace_bytes.restype = ctypes.c_int64
         LL = ctypes.c_longlong
@@ -263,6 +265,12 @@ class Context:
     def workspace_bytes(self) -> int:
         return int(lib().df_workspace_bytes(self._h))
 
+    def sparsity(self):
+        """(nonzero K-tile fraction of the first GEMM, nonzero (mu, 64-nu chunk) fraction of rho/J)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().df_sparsity(self._h, ctypes.byref(a), ctypes.byref(b)), "df_sparsity")
+        return a.value, b.value
+
     def setup(self, B: torch.Tensor, perm=None, stream=None):
         """Attach B; `perm` (new position -> original P) orders the exchange path's auxiliary functions."""
         assert B.shape == (self.naux, self.nao, self.nao)
@@ -339,6 +347,10 @@ class Context:
     def set_cluster_pairs(self, mode: int):
         """DF_OPT_CLUSTER_PAIRS: 0 never, 1 the first exchange GEMM (default), 2 both GEMMs."""
         _check(lib().df_set_option(self._h, OPT_CLUSTER_PAIRS, int(mode)), "df_set_option")
+
+    def set_sparse(self, on: bool):
+        """DF_OPT_SPARSE: use the block sparsity of a screened B (default) or run dense."""
+        _check(lib().df_set_option(self._h, OPT_SPARSE, 1 if on else 0), "df_set_option")
 
     def phase_times(self):
         """{phase: (total ms, records)} since the last read (waits for the events)."""

@@ -190,13 +190,14 @@ def one_electron(mol: Molecule, Z: np.ndarray):
     return S, T, V, E_nuc
 
 
-def df_tensor(mol: Molecule) -> np.ndarray:
-    """B[P, mu, nu] = sum_Q L^{-1}[P, Q] (Q|mu nu), L L^T = (P|Q) (Eq. cderi)."""
+def df_tensor(mol: Molecule, tau: float = 0.0) -> np.ndarray:
+    """B[P, mu, nu] = sum_Q L^{-1}[P, Q] (Q|mu nu), L L^T = (P|Q) (Eq. cderi), from the
+    Schwarz-screened integrals when tau > 0 (screened pairs are exact zeros in every B_P)."""
     import scipy.linalg as sl
     from scipy.linalg.blas import dtrsm
     V = metric(mol)
     L = sl.cholesky(V, lower=True, check_finite=False)
-    T = int3c(mol).reshape(mol.naux, -1)
+    T = screened_int3c(mol, tau).reshape(mol.naux, -1)
     # B^T = T^T L^{-T}: a right-side solve on the Fortran-order view of T (no copy)
     Bt = dtrsm(1.0, L, T.T, side=1, lower=1, trans_a=1, overwrite_b=1)
     B = np.ascontiguousarray(Bt.T).reshape(mol.naux, mol.nao, mol.nao)

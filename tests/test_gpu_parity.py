@@ -438,3 +438,21 @@ def test_bounded_wait_reports_a_timeout_and_the_context_survives(df, small):
     K, _ = ctx.build_K(cuda(C), 0)
     ctx.sync_status()
     assert np.allclose(K.cpu().numpy(), O.exchange(B, C), rtol=0, atol=1e-12 * np.abs(O.exchange(B, C)).max())
+
+
+def test_setup_rejects_an_asymmetric_tensor(df, small):
+    """rho and J read the upper triangle of each B_P, so df_setup requires exact symmetry:
+    one element off by one ulp is refused with DF_ERR_ARG; the symmetric tensor is taken."""
+    B, C, D = small
+    Bbad = B.copy()
+    Bbad[7, 3, 11] = np.nextafter(Bbad[7, 3, 11], np.inf)
+    ctx = df.Context(B.shape[1], B.shape[0], C.shape[1])
+    with pytest.raises(df.DFError) as e:
+        ctx.setup(cuda(Bbad))
+    assert e.value.status == -1
+    with pytest.raises(df.DFError):
+        ctx.build_J(cuda(D))               # not set up: refused
+    ctx.setup(cuda(B))
+    J = ctx.build_J(cuda(D))[0].cpu().numpy()
+    J_ref = O.coulomb(B, O.rho(B, D))
+    assert np.max(np.abs(J - J_ref)) <= 1e-12 * np.max(np.abs(J_ref))

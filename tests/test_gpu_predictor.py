@@ -279,7 +279,7 @@ def test_ordered_setup_matches_oracle_on_permuted_tensor(df, small_ctx):
 
 
 def test_learned_counts_state_the_gain_on_a_held_out_molecule(df):
-    """The learned part's gain, stated.  Train on six molecules of 20-38 atoms (labels: per
+    """The learned part's gain, stated.  Train on twelve molecules of 20-40 atoms (labels: per
     level, the fewest slice pairs whose summed block errors stay within the rule's), then
     run the library's learned mode on a held-out 36-atom molecule at every level.
 
@@ -291,7 +291,8 @@ def test_learned_counts_state_the_gain_on_a_held_out_molecule(df):
     themselves save under 5 % of the rule's slice pairs, and the network saves no more."""
     from paper_2601_08077_gb300 import predictor
     train, keep = [], []
-    for atoms, seed in [(20, 21), (26, 22), (30, 23), (34, 24), (24, 25), (38, 26)]:
+    for atoms, seed in [(20, 21), (26, 22), (30, 23), (34, 24), (24, 25), (38, 26), (22, 27), (28, 28),
+                        (32, 29), (36, 30), (40, 33), (21, 34)]:
         mol = inputs.molecule(atoms, seed)
         B = inputs.df_tensor_device(mol)
         ctx = df.Context(mol.nao, mol.naux, atoms)
@@ -303,7 +304,7 @@ def test_learned_counts_state_the_gain_on_a_held_out_molecule(df):
     F = torch.cat([t[0] for t in train])
     y = torch.cat([t[1] for t in train])
     p = predictor.SlicePredictor(seed=0)
-    hist = p.fit(F, y, steps=1500, lr=3e-3)
+    hist = p.fit(F, y, steps=2500, lr=3e-3)
     assert hist[-1] < hist[0]
     mol = inputs.molecule(36, 31)
     B = inputs.df_tensor_device(mol)
@@ -335,4 +336,4 @@ def test_learned_counts_state_the_gain_on_a_held_out_molecule(df):
     print("slice pairs: rule %(rule)d, labels %(labels)d, learned %(learned)d" % work,
           "recomputed %d; gain labels %.3f learned %.3f" % (recomputed, gain_labels, gain_learned))
     assert 0.0 <= gain_labels < 0.05
-    assert -0.10 < gain_learned < 0.05
+    assert -0.10 < gain_learned < 0.05      # no gain; at most the cost of a few misplaced counts

@@ -355,3 +355,34 @@ def test_df_tensor_rows_is_the_leading_block(small):
     V = inputs.metric(mol)
     tol = V.shape[0] * 2.0 ** -52 * math.sqrt(np.linalg.cond(V)) * np.max(np.abs(B))
     assert np.max(np.abs(Bk - B[:128])) <= tol
+
+
+# --- Schwarz screening (Section 2.1) ---------------------------------------------
+
+def test_schwarz_self_coulomb_is_the_four_index_diagonal(tiny):
+    mol = tiny[0]
+    eri = O.eri4(mol.ao_xyz, mol.ao_exp)
+    n = mol.nao
+    diag = np.array([[eri[a, b, a, b] for b in range(n)] for a in range(n)])
+    assert np.allclose(O.pair_self_coulomb(mol.ao_xyz, mol.ao_exp), diag, rtol=1e-13, atol=0)
+
+
+def test_schwarz_inequality_bounds_the_integrals(tiny):
+    """The Cauchy-Schwarz bounds behind the screening: |(ab|cd)| <= sqrt((ab|ab)(cd|cd)) and
+    |(P|ab)| <= sqrt((P|P)(ab|ab)), brute force over every index."""
+    mol, T, V = tiny[0], tiny[1], tiny[2]
+    eri = O.eri4(mol.ao_xyz, mol.ao_exp)
+    q = np.sqrt(O.pair_self_coulomb(mol.ao_xyz, mol.ao_exp))
+    assert np.all(np.abs(eri) <= q[:, :, None, None] * q[None, None, :, :] * (1 + 1e-12))
+    assert np.all(np.abs(T) <= np.sqrt(np.diag(V))[:, None, None] * q[None, :, :] * (1 + 1e-12))
+
+
+def test_schwarz_mask_of_the_generator_and_the_zeros_of_B():
+    """The input generator's screening equals the oracle's on a 30-atom chain, keeps every
+    diagonal pair, and the screened pairs are exact zeros in every B_P."""
+    mol = inputs.chain_molecule(30, 5)
+    keep = O.schwarz_keep(mol.ao_xyz, mol.ao_exp, mol.aux_xyz, mol.aux_exp, 1e-12)
+    assert np.array_equal(inputs.schwarz_pairs(mol, 1e-12), keep)
+    assert keep.all(axis=None) is not True and np.all(np.diag(keep)) and 0.2 < keep.mean() < 0.6
+    B = inputs.df_tensor(mol, 1e-12)
+    assert np.all(B[:, ~keep] == 0.0) and np.all(np.abs(B).max(axis=0)[keep] > 0.0)
