@@ -28,8 +28,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One CTA per P.  Warp w takes rows mu = w, w + 8, ...; lanes stride nu >= mu
-// (with masks: over the nonzero 64-wide chunks of the row only).
+// One CTA per P.  Warp w takes rows mu = w, w + 8, ...; lanes stride nu >= mu.
+// With masks a lane skips the nu of zero chunks (no load: the bytes are not
+// fetched) and keeps the dense order of the rest, so rho is bit-identical to
+// the dense sum (a skipped term is an exact zero).
 __global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, const double *__restrict__ D,
                                                   int nao, double *__restrict__ rho,
                                                   const uint32_t *__restrict__ mask_mu) {
@@ -41,16 +43,9 @@ __global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, 
     const double *brow = BP + (long long)mu * nao;
     const double *drow = D + (long long)mu * nao;
     if (lane == 0) dia = fma(__ldg(brow + mu), __ldg(drow + mu), dia);
-    if (mask_mu) {
-      const uint32_t mk = __ldg(mask_mu + mu);
-      for (int c = (mu + 1) >> 6; c * 64 < nao; ++c) {
-        if (!((mk >> c) & 1u)) continue;
-        const int hi = min(nao, c * 64 + 64);
-        for (int nu = max(mu + 1, c * 64) + lane; nu < hi; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
-      }
-    } else {
-      for (int nu = mu + 1 + lane; nu < nao; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
-    }
+    const uint32_t mk = mask_mu ? __ldg(mask_mu + mu) : 0xFFFFFFFFu;
+    for (int nu = mu + 1 + lane; nu < nao; nu += 32)
+      if ((mk >> (nu >> 6)) & 1u) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
   }
   double v = 2.0 * off + dia;
   v = warp_sum(v);
