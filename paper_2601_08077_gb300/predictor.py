@@ -11,7 +11,7 @@ auxiliary block b the K_b error of the emulated build at every slice count
 (df_block_errors), and, per Table 1 level L with count s_L, the per-block
 counts with the fewest slice pairs whose summed block errors stay within the
 rule's own: sum_b err_b(s_b) <= sum_b err_b(s_L).  The network thereby
-serves the accuracy the rule (the judge) achieves at that level, and can only
+serves the accuracy the rule itself achieves at that level, and can only
 save work by trading: more slices on blocks whose errors dominate, fewer on
 blocks whose errors are negligible.
 """
