@@ -91,6 +91,16 @@ df_status df_setup(df_ctx *ctx, const double *B_dev, void *stream);
  * NULL = the natural order.  DF_ERR_ARG if perm_host is not a permutation. */
 df_status df_setup_ordered(df_ctx *ctx, const double *B_dev, const int *perm_host, void *stream);
 
+/* As df_setup_ordered, with B given packed: Bp_dev [naux][nao (nao + 1) / 2]
+ * holds each B_P's upper triangle row by row (element (mu, nu), nu >= mu, at
+ * mu nao - mu (mu - 1) / 2 + nu - mu), the symmetric storage Section 3.3
+ * describes, half the bytes of the dense tensor.  Caller-owned and kept alive
+ * for the context's lifetime.  rho and J read it directly (bit-identical to a
+ * dense B with the same values), the digit planes and the sparsity masks are
+ * formed from it, and the native FP64 comparison build unpacks it in chunks
+ * of about 1 GB (stream-ordered scratch).  Synchronises `stream`. */
+df_status df_setup_packed(df_ctx *ctx, const double *Bp_dev, const int *perm_host, void *stream);
+
 /* As df_setup_ordered, forming B on the device from the integrals
  * (Eq. cderi): B = L^{-1} (P|mu nu) with L L^T = (P|Q) the metric's Cholesky
  * factor.  T_dev [naux][nao][nao] holds (P|mu nu) on entry and B on return
@@ -333,8 +343,9 @@ df_status df_block_features(df_ctx *ctx, int nocc, double tau, double dD, double
  * largest exponent of the block's X rows, F_b of its B rows, E_c of C's
  * columns; the first term bounds the slice truncation of both GEMMs, the
  * second the FP64 roundings): the counts pass if
- * sum_b beta_b(s_b) <= sum_b beta_b(s_L), i.e. the learned build's bound is
- * at most the rule's.  Otherwise the blocks with s_b < s_L are raised to s_L,
+ * sum_b beta_b(s_b) <= (1 + 1e-12) sum_b beta_b(s_L), i.e. the learned
+ * build's bound is at most the rule's (the 1e-12 absorbs the rounding of the
+ * sums; a block whose bound is that far below the others may keep any count).  Otherwise the blocks with s_b < s_L are raised to s_L,
  * largest beta_b(s_b) first, until it holds, and the first GEMM and the X
  * split are run again with the raised counts. */
 df_status df_set_predictor(df_ctx *ctx, df_mlp *net, float min_conf);

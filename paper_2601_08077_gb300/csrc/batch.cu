@@ -248,8 +248,9 @@ df_status df_batch_build_J(df_batch *b, const double *const *D, double *const *J
       df_ctx *c = b->ctx[i];
       if (!c->ready) return DF_ERR_STATE;
       const uint32_t *mk = df::use_mask_mu(c);
-      if (df::launch_rho(c->B, D[i], c->naux, c->nao, c->rho, st, mk) != cudaSuccess) return DF_ERR_CUDA;
-      if (df::launch_coulomb(c->B, c->rho, c->naux, c->nao, J[i], st, mk) != cudaSuccess) return DF_ERR_CUDA;
+      if (df::launch_rho(c->B, D[i], c->naux, c->nao, c->rho, st, mk, c->packed) != cudaSuccess) return DF_ERR_CUDA;
+      if (df::launch_coulomb(c->B, c->rho, c->naux, c->nao, J[i], st, mk, c->packed) != cudaSuccess)
+        return DF_ERR_CUDA;
     }
     return DF_OK;
   };
@@ -263,7 +264,8 @@ df_status df_batch_build_J(df_batch *b, const double *const *D, double *const *J
     drop_graph(b->exec_J);
     // the Coulomb kernel sets its shared-memory attribute on first use: do it outside capture
     for (int i = 0; i < n; ++i)
-      if (df::launch_coulomb(b->ctx[i]->B, b->ctx[i]->rho, b->ctx[i]->naux, b->ctx[i]->nao, J[i], st) !=
+      if (df::launch_coulomb(b->ctx[i]->B, b->ctx[i]->rho, b->ctx[i]->naux, b->ctx[i]->nao, J[i], st, nullptr,
+                             b->ctx[i]->packed) !=
           cudaSuccess)
         return DF_ERR_CUDA;
     cudaGraph_t graph = nullptr;

@@ -12,6 +12,11 @@
 // bounded by FP64 FMA throughput rather than by HBM; the roofline reported
 // for them uses the measured FP64 rate.
 //
+// B comes dense ([naux][nao][nao]) or packed (per P the upper triangle row by
+// row, [naux][nao (nao + 1) / 2], the symmetric storage Section 3.3
+// describes); both layouts are read in the same order, so rho and J are
+// bit-identical between them.
+//
 // A Schwarz-screened B (Section 2.1: a screened AO pair is zero in every B_P)
 // is block-sparse: with per-mu masks of the 64-wide nu chunks that hold a
 // nonzero, both passes skip the zero chunks (rho loses only zero terms; J is
@@ -21,6 +26,11 @@
 namespace df {
 
 namespace {
+
+// Start of row mu in a packed upper triangle of order nao.
+__device__ __forceinline__ long long packed_row(int mu, int nao) {
+  return (long long)mu * nao - (long long)mu * (mu - 1) / 2;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -32,20 +42,31 @@ __device__ __forceinline__ double warp_sum(double v) {
 // With masks a lane skips the nu of zero chunks (no load: the bytes are not
 // fetched) and keeps the dense order of the rest, so rho is bit-identical to
 // the dense sum (a skipped term is an exact zero).
+template <bool kPacked>
 __global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, const double *__restrict__ D,
                                                   int nao, double *__restrict__ rho,
                                                   const uint32_t *__restrict__ mask_mu) {
   const int P = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double *BP = B + (long long)P * nao * nao;
+  const double *BP = B + (long long)P * (kPacked ? (long long)nao * (nao + 1) / 2 : (long long)nao * nao);
   double off = 0.0, dia = 0.0;
   for (int mu = warp; mu < nao; mu += 8) {
-    const double *brow = BP + (long long)mu * nao;
+    // brow[nu] is B_P mu nu for nu >= mu in either layout
+    const double *brow = kPacked ? BP + packed_row(mu, nao) - mu : BP + (long long)mu * nao;
     const double *drow = D + (long long)mu * nao;
     if (lane == 0) dia = fma(__ldg(brow + mu), __ldg(drow + mu), dia);
-    const uint32_t mk = mask_mu ? __ldg(mask_mu + mu) : 0xFFFFFFFFu;
-    for (int nu = mu + 1 + lane; nu < nao; nu += 32)
-      if ((mk >> (nu >> 6)) & 1u) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+    if (!mask_mu) {
+      for (int nu = mu + 1 + lane; nu < nao; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+    } else {
+      // the warp's 32-wide windows of the dense loop; a window whose one or two
+      // chunks are all zero is skipped as a whole (no loads)
+      const uint32_t mk = __ldg(mask_mu + mu);
+      for (int base = mu + 1; base < nao; base += 32) {
+        if (!(((mk >> (base >> 6)) | (mk >> ((base + 31) >> 6))) & 1u)) continue;
+        const int nu = base + lane;
+        if (nu < nao && ((mk >> (nu >> 6)) & 1u)) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+      }
+    }
   }
   double v = 2.0 * off + dia;
   v = warp_sum(v);
@@ -64,6 +85,7 @@ __global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, 
 // column y, then row nao-1-y from its diagonal (nao + 1 elements per pair, one
 // row alone in the middle when nao is odd), so every CTA has the same work.
 // Each element's sum runs over P in ascending order, one FMA per P.
+template <bool kPacked>
 __global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__ B, const double *__restrict__ rho,
                                                       int naux, int nao, double *__restrict__ J,
                                                       const uint32_t *__restrict__ mask_mu) {
@@ -76,11 +98,12 @@ __global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__
   if (e >= len0 + len1) return;
   const int mu = e < len0 ? m0 : m1;
   const int nu = e < len0 ? m0 + e : m1 + (e - len0);
-  const long long off = (long long)mu * nao + nu;
-  const long long stride = (long long)nao * nao;
+  const long long off = kPacked ? packed_row(mu, nao) + (nu - mu) : (long long)mu * nao + nu;
+  const long long stride = kPacked ? (long long)nao * (nao + 1) / 2 : (long long)nao * nao;
+  const long long jmn = (long long)mu * nao + nu;
   if (mask_mu && !((__ldg(mask_mu + mu) >> (nu >> 6)) & 1u)) {
     // a screened pair: B_P mu nu = 0 for every P
-    J[off] = 0.0;
+    J[jmn] = 0.0;
     J[(long long)nu * nao + mu] = 0.0;
     return;
   }
@@ -97,7 +120,7 @@ __global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__
     acc = fma(b3, srho[P + 3], acc);
   }
   for (; P < naux; ++P) acc = fma(__ldg(B + P * stride + off), srho[P], acc);
-  J[off] = acc;
+  J[jmn] = acc;
   J[(long long)nu * nao + mu] = acc;
 }
 
@@ -227,6 +250,42 @@ __global__ void __launch_bounds__(256) pair_mask_kernel(const double *__restrict
   }
 }
 
+// Packed B: flag[k] = 1 when the packed pair k (of the upper triangle) is
+// nonzero in some B_P (one coalesced pass over B), then the per-mu masks
+// over all nu from the symmetric pair flags.
+__global__ void __launch_bounds__(256) packed_pair_flags_kernel(const double *__restrict__ Bp, int naux,
+                                                                long long npk, uint8_t *__restrict__ flag) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npk) return;
+  uint8_t f = 0;
+  for (int P = 0; P < naux && !f; ++P) f = __ldg(Bp + (long long)P * npk + k) != 0.0;
+  flag[k] = f;
+}
+
+__global__ void mask_from_packed_flags_kernel(const uint8_t *__restrict__ flag, int nao,
+                                              uint32_t *__restrict__ mask_mu) {
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mu >= nao) return;
+  uint32_t bits = 0u;
+  for (int nu = 0; nu < nao; ++nu) {
+    const long long k = nu >= mu ? packed_row(mu, nao) + (nu - mu) : packed_row(nu, nao) + (mu - nu);
+    if (flag[k]) bits |= 1u << (nu >> 6);
+  }
+  mask_mu[mu] = bits;
+}
+
+// Dense copy of B_P for P = P0 .. P0 + nP - 1 from the packed layout.
+__global__ void unpack_kernel(const double *__restrict__ Bp, int P0, int nP, int nao, double *__restrict__ out) {
+  const long long npk = (long long)nao * (nao + 1) / 2;
+  const long long n2 = (long long)nao * nao;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nP * n2) return;
+  const int pl = (int)(i / n2);
+  const int mu = (int)((i - pl * n2) / nao), nu = (int)(i - pl * n2 - (long long)mu * nao);
+  const int lo = mu < nu ? mu : nu, hi = mu < nu ? nu : mu;
+  out[i] = __ldg(Bp + (long long)(P0 + pl) * npk + packed_row(lo, nao) + (hi - lo));
+}
+
 // Per 128-row tile t of the (P, mu) rows (row r has mu = r mod nao): the OR of
 // its rows' masks.
 __global__ void tile_mask_kernel(const uint32_t *__restrict__ mask_mu, int nao, long long rows, int ntiles,
@@ -242,6 +301,34 @@ __global__ void tile_mask_kernel(const uint32_t *__restrict__ mask_mu, int nao, 
 }  // namespace
 
 constexpr int kEnergyBlocks = 296;
+
+cudaError_t launch_pair_masks_packed(const double *Bp, int naux, int nao, uint32_t *mask_mu, uint32_t *mask_tile,
+                                     cudaStream_t st) {
+  const long long npk = (long long)nao * (nao + 1) / 2;
+  uint8_t *flag = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&flag), (size_t)npk, st);
+  if (e != cudaSuccess) return e;
+  packed_pair_flags_kernel<<<(unsigned)((npk + 255) / 256), 256, 0, st>>>(Bp, naux, npk, flag);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    mask_from_packed_flags_kernel<<<(nao + 127) / 128, 128, 0, st>>>(flag, nao, mask_mu);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const long long rows = (long long)naux * nao;
+    const int ntiles = (int)((rows + kTile - 1) / kTile);
+    tile_mask_kernel<<<(ntiles + 255) / 256, 256, 0, st>>>(mask_mu, nao, rows, ntiles, mask_tile);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(flag, st);
+  return e;
+}
+
+cudaError_t launch_unpack(const double *Bp, int P0, int nP, int nao, double *out, cudaStream_t st) {
+  const long long n = (long long)nP * nao * nao;
+  unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Bp, P0, nP, nao, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_symmetry_check(const double *B, int naux, int nao, int *flag, cudaStream_t st) {
   const int nt = (nao + 31) / 32;
@@ -279,22 +366,30 @@ cudaError_t launch_density_change(const double *D, double *Dprev, bool have_prev
 }
 
 cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st,
-                       const uint32_t *mask_mu) {
-  rho_kernel<<<naux, 256, 0, st>>>(B, D, nao, rho, mask_mu);
+                       const uint32_t *mask_mu, bool packed) {
+  if (packed)
+    rho_kernel<true><<<naux, 256, 0, st>>>(B, D, nao, rho, mask_mu);
+  else
+    rho_kernel<false><<<naux, 256, 0, st>>>(B, D, nao, rho, mask_mu);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st,
-                           const uint32_t *mask_mu) {
+                           const uint32_t *mask_mu, bool packed) {
   const size_t sm = (size_t)naux * sizeof(double);
   static size_t attr = 48 * 1024;
   if (sm > attr) {
-    cudaError_t e = cudaFuncSetAttribute(coulomb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(coulomb_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(coulomb_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr = sm;
   }
   dim3 grid((nao + 1 + 255) / 256, (nao + 1) / 2);
-  coulomb_kernel<<<grid, 256, sm, st>>>(B, rho, naux, nao, J, mask_mu);
+  if (packed)
+    coulomb_kernel<true><<<grid, 256, sm, st>>>(B, rho, naux, nao, J, mask_mu);
+  else
+    coulomb_kernel<false><<<grid, 256, sm, st>>>(B, rho, naux, nao, J, mask_mu);
   return cudaGetLastError();
 }
 

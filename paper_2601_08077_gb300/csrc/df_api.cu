@@ -11,6 +11,7 @@
 // cuBLAS DGEMM (strided batched over P) and DSYRK.
 #include "df_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -111,10 +112,29 @@ df_status build_K_fp64(df_ctx *c, const double *C, int nocc, double *K, cudaStre
   // C^T B_P lands at Xt + P*nocc with leading dimension naux*nocc.
   {
     PhaseTimer t(c, DF_PHASE_GEMM1, st);
-    cublasStatus_t s1 = cublasDgemmStridedBatched(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, nocc, c->nao, c->nao, &one,
-                                                  C, nocc, 0, c->B, c->nao, (long long)c->nao * c->nao, &zero, c->X,
-                                                  (int)ldx, nocc, c->naux);
-    if (s1 != CUBLAS_STATUS_SUCCESS) return record(c, DF_ERR_CUDA);
+    const long long n2 = (long long)c->nao * c->nao;
+    if (!c->packed) {
+      cublasStatus_t s1 = cublasDgemmStridedBatched(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, nocc, c->nao, c->nao, &one,
+                                                    C, nocc, 0, c->B, c->nao, n2, &zero, c->X, (int)ldx, nocc,
+                                                    c->naux);
+      if (s1 != CUBLAS_STATUS_SUCCESS) return record(c, DF_ERR_CUDA);
+    } else {
+      // packed B: dense copies of up to ~1 GB of B_P at a time
+      const int chunk = (int)std::max<long long>(1, std::min<long long>(c->naux, (1ll << 27) / n2));
+      double *dense = nullptr;
+      DF_TRY(c, cudaMallocAsync(reinterpret_cast<void **>(&dense), sizeof(double) * n2 * chunk, st));
+      df_status rs = DF_OK;
+      for (int P0 = 0; P0 < c->naux && rs == DF_OK; P0 += chunk) {
+        const int nP = std::min(chunk, c->naux - P0);
+        if (df::launch_unpack(c->B, P0, nP, c->nao, dense, st) != cudaSuccess ||
+            cublasDgemmStridedBatched(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, nocc, c->nao, c->nao, &one, C, nocc, 0,
+                                      dense, c->nao, n2, &zero, c->X + (long long)P0 * nocc, (int)ldx, nocc,
+                                      nP) != CUBLAS_STATUS_SUCCESS)
+          rs = DF_ERR_CUDA;
+      }
+      cudaFreeAsync(dense, st);
+      if (rs != DF_OK) return record(c, rs);
+    }
   }
   PhaseTimer t2(c, DF_PHASE_GEMM2, st);
   cublasStatus_t s2 = cublasDsyrk(c->cublas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, c->nao, (int)ldx, &one, c->X,
@@ -525,10 +545,15 @@ df_status df_last_error(const df_ctx *c) { return c ? c->last : DF_ERR_ARG; }
 
 df_status df_setup(df_ctx *c, const double *B_dev, void *stream) { return df_setup_ordered(c, B_dev, nullptr, stream); }
 
-df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host, void *stream) {
+namespace {
+
+// df_setup_ordered / df_setup_packed: attach B (dense, or packed upper
+// triangles), check it, split it and find its block sparsity.
+df_status setup_common(df_ctx *c, const double *B_dev, const int *perm_host, bool packed, void *stream) {
   if (!c || !B_dev) return record(c, DF_ERR_ARG);
   cudaStream_t st = as_stream(stream);
   c->B = B_dev;
+  c->packed = packed;
   if (perm_host) {
     std::vector<char> seen(c->naux, 0);
     for (int i = 0; i < c->naux; ++i) {
@@ -548,8 +573,8 @@ df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host,
     c->bstats = nullptr;
   }
   c->ready = false;
-  // rho and J read the upper triangle of each B_P: B_P must be exactly symmetric
-  {
+  // rho and J read the upper triangle of each B_P: a dense B_P must be exactly symmetric
+  if (!packed) {
     int h = 0;
     DF_TRY(c, df::launch_symmetry_check(B_dev, c->naux, c->nao, c->status, st));
     DF_TRY(c, cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -558,8 +583,12 @@ df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host,
     if (h) return record(c, DF_ERR_ARG);
   }
   const long long rows = (long long)c->naux * c->nao;
-  DF_TRY(c, df::launch_split_rows_bf16(B_dev, rows, c->nao, c->nao, c->s_max, c->eB, c->Bd, c->ld_nao,
-                                       rows * c->ld_nao, st, c->perm, c->nao));
+  if (packed)
+    DF_TRY(c, df::launch_split_rows_packed(B_dev, c->naux, c->nao, c->s_max, c->eB, c->Bd, c->ld_nao,
+                                           rows * c->ld_nao, c->perm, st));
+  else
+    DF_TRY(c, df::launch_split_rows_bf16(B_dev, rows, c->nao, c->nao, c->s_max, c->eB, c->Bd, c->ld_nao,
+                                         rows * c->ld_nao, st, c->perm, c->nao));
   // block sparsity of a screened B (Section 2.1): exact zero chunks of the AO pairs
   c->sparse = false;
   c->frac_ktiles = c->frac_chunks = 1.0;
@@ -567,7 +596,10 @@ df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host,
     const int ntiles = (int)((rows + df::kTile - 1) / df::kTile);
     if (!c->mask_mu) DF_TRY(c, cudaMalloc(&c->mask_mu, sizeof(uint32_t) * c->nao));
     if (!c->mask_tile) DF_TRY(c, cudaMalloc(&c->mask_tile, sizeof(uint32_t) * ntiles));
-    DF_TRY(c, df::launch_pair_masks(B_dev, c->naux, c->nao, c->mask_mu, c->mask_tile, st));
+    if (packed)
+      DF_TRY(c, df::launch_pair_masks_packed(B_dev, c->naux, c->nao, c->mask_mu, c->mask_tile, st));
+    else
+      DF_TRY(c, df::launch_pair_masks(B_dev, c->naux, c->nao, c->mask_mu, c->mask_tile, st));
     std::vector<uint32_t> mu(c->nao), tiles(ntiles);
     DF_TRY(c, cudaMemcpyAsync(mu.data(), c->mask_mu, sizeof(uint32_t) * c->nao, cudaMemcpyDeviceToHost, st));
     DF_TRY(c, cudaMemcpyAsync(tiles.data(), c->mask_tile, sizeof(uint32_t) * ntiles, cudaMemcpyDeviceToHost, st));
@@ -588,6 +620,16 @@ df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host,
   return DF_OK;
 }
 
+}  // namespace
+
+df_status df_setup_ordered(df_ctx *c, const double *B_dev, const int *perm_host, void *stream) {
+  return setup_common(c, B_dev, perm_host, false, stream);
+}
+
+df_status df_setup_packed(df_ctx *c, const double *Bp_dev, const int *perm_host, void *stream) {
+  return setup_common(c, Bp_dev, perm_host, true, stream);
+}
+
 df_status df_build_J(df_ctx *c, const double *D, double *J, double *rho, void *stream) {
   if (!c || !D || !J) return record(c, DF_ERR_ARG);
   if (!c->ready) return record(c, DF_ERR_STATE);
@@ -595,11 +637,11 @@ df_status df_build_J(df_ctx *c, const double *D, double *J, double *rho, void *s
   double *r = rho ? rho : c->rho;
   {
     PhaseTimer t(c, DF_PHASE_RHO, st);
-    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, r, st, df::use_mask_mu(c)));
+    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, r, st, df::use_mask_mu(c), c->packed));
   }
   {
     PhaseTimer t(c, DF_PHASE_COULOMB, st);
-    DF_TRY(c, df::launch_coulomb(c->B, r, c->naux, c->nao, J, st, df::use_mask_mu(c)));
+    DF_TRY(c, df::launch_coulomb(c->B, r, c->naux, c->nao, J, st, df::use_mask_mu(c), c->packed));
   }
   if (rho && rho != c->rho)
     DF_TRY(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * c->naux, cudaMemcpyDeviceToDevice, st));

@@ -9,7 +9,8 @@ struct df_ctx {
   int nao = 0, naux = 0, nocc_max = 0, s_max = 0, nblk = 0;
   long long ld_nao = 0;    // row stride (elements) of the B and C digit rows
   long long kb_ld_max = 0; // row stride bound of the X digit rows
-  const double *B = nullptr;
+  const double *B = nullptr;  // dense [naux][nao][nao], or packed [naux][nao (nao + 1) / 2]
+  bool packed = false;
   bool ready = false;
   uint16_t *Bd = nullptr;
   int *eB = nullptr;

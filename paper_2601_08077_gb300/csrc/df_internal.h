@@ -156,10 +156,19 @@ int fixed_point_shift(int s, long long k);
 
 // mask_mu (optional, block-sparse B): per mu, bit c set when some B_P mu nu
 // with nu in [64c, 64c + 64) is nonzero; null = dense.
+// packed: B holds per P the upper triangle row by row ([naux][nao (nao + 1) / 2]).
 cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st,
-                       const uint32_t *mask_mu = nullptr);
+                       const uint32_t *mask_mu = nullptr, bool packed = false);
 cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st,
-                           const uint32_t *mask_mu = nullptr);
+                           const uint32_t *mask_mu = nullptr, bool packed = false);
+// The masks of a packed B (pair flags through stream-ordered scratch of nao (nao + 1) / 2 bytes).
+cudaError_t launch_pair_masks_packed(const double *Bp, int naux, int nao, uint32_t *mask_mu, uint32_t *mask_tile,
+                                     cudaStream_t st);
+// Dense B_P, P = P0 .. P0 + nP - 1, into out [nP][nao][nao] from a packed B.
+cudaError_t launch_unpack(const double *Bp, int P0, int nP, int nao, double *out, cudaStream_t st);
+// Digits of B from its packed layout (rows (P', mu) as launch_split_rows_bf16 writes them).
+cudaError_t launch_split_rows_packed(const double *Bp, int naux, int nao, int nslices, int *exps, uint16_t *digits,
+                                     long long dld, long long plane_stride, const int *perm, cudaStream_t st);
 // Sets *flag (zeroed first) when some B_P of B [naux][nao][nao] is not exactly
 // symmetric.
 cudaError_t launch_symmetry_check(const double *B, int naux, int nao, int *flag, cudaStream_t st);

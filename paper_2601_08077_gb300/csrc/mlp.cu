@@ -154,21 +154,37 @@ __global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ G, 
 // Static per-block statistics of B: [0] max|B|, [1] sum B^2, [2] sum of row
 // exponents over nonzero rows, [3] nonzero rows, [4] min exponent, [5] max
 // exponent, [6] rows with exponent < max_e - 20 (filled in a second pass).
+// packed: B holds per P the upper triangle row by row (off-diagonal entries
+// then count twice in the sum of squares).
 __global__ void __launch_bounds__(256) block_stats_kernel(const double *__restrict__ B, const int *__restrict__ eB,
                                                           const int *__restrict__ perm, int naux, int nao,
-                                                          double *__restrict__ stats) {
+                                                          double *__restrict__ stats, bool packed) {
   const int b = blockIdx.x;
   const int p0 = b * df::kBlock;
   const int nP = min(df::kBlock, naux - p0);
   const long long n2 = (long long)nao * nao;
+  const long long npk = (long long)nao * (nao + 1) / 2;
   double mx = 0.0, ss = 0.0;
   for (int pl = 0; pl < nP; ++pl) {
     const int P = perm ? perm[p0 + pl] : p0 + pl;
-    const double *src = B + (long long)P * n2;
-    for (long long i = threadIdx.x; i < n2; i += blockDim.x) {
-      const double v = src[i];
-      mx = fmax(mx, fabs(v));
-      ss = fma(v, v, ss);
+    if (packed) {
+      const double *src = B + (long long)P * npk;
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int mu = warp; mu < nao; mu += (int)(blockDim.x >> 5)) {
+        const double *row = src + (long long)mu * nao - (long long)mu * (mu - 1) / 2 - mu;
+        for (int nu = mu + lane; nu < nao; nu += 32) {
+          const double v = row[nu];
+          mx = fmax(mx, fabs(v));
+          ss = fma(nu == mu ? v : 2.0 * v, v, ss);
+        }
+      }
+    } else {
+      const double *src = B + (long long)P * n2;
+      for (long long i = threadIdx.x; i < n2; i += blockDim.x) {
+        const double v = src[i];
+        mx = fmax(mx, fabs(v));
+        ss = fma(v, v, ss);
+      }
     }
   }
   double esum = 0.0, cnt = 0.0, emin = 1e9, emax = -1e9;
@@ -433,7 +449,7 @@ df_status df_block_features(df_ctx *c, int nocc, double tau, double dD, double d
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (!c->bstats) {
     if (cudaMalloc(&c->bstats, sizeof(double) * 8 * c->nblk) != cudaSuccess) return DF_ERR_OOM;
-    block_stats_kernel<<<c->nblk, 256, 0, st>>>(c->B, c->eB, c->perm, c->naux, c->nao, c->bstats);
+    block_stats_kernel<<<c->nblk, 256, 0, st>>>(c->B, c->eB, c->perm, c->naux, c->nao, c->bstats, c->packed);
     if (cudaGetLastError() != cudaSuccess) return DF_ERR_CUDA;
   }
   block_features_kernel<<<(c->nblk + 127) / 128, 128, 0, st>>>(c->bstats, c->nblk, c->naux, c->nao, nocc, tau, dD,
@@ -574,7 +590,7 @@ df_status build_K_learned(df_ctx *c, const double *C, int nocc, double *K, df_ks
   if (e == cudaSuccess && !c->bstats) {
     e = cudaMalloc(&c->bstats, sizeof(double) * 8 * nblk);
     if (e == cudaSuccess) {
-      block_stats_kernel<<<nblk, 256, 0, st>>>(c->B, c->eB, c->perm, c->naux, c->nao, c->bstats);
+      block_stats_kernel<<<nblk, 256, 0, st>>>(c->B, c->eB, c->perm, c->naux, c->nao, c->bstats, c->packed);
       e = cudaGetLastError();
     }
   }

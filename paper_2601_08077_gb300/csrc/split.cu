@@ -118,6 +118,61 @@ __global__ void __launch_bounds__(256) split_rows_bf16_kernel(const double *__re
   }
 }
 
+// Rows of B from its packed layout (per P the upper triangle row by row,
+// nao (nao + 1) / 2 values): output row r = (P', mu), P = perm[P'] (or P'),
+// holds B_P mu nu for every nu (nu < mu read at the transposed position).
+// One warp per row; the same two passes and digits as split_rows_bf16_kernel.
+__global__ void __launch_bounds__(256) split_rows_packed_kernel(const double *__restrict__ Bp, long long rows,
+                                                                int nao, int nslices, int *__restrict__ exps,
+                                                                uint16_t *__restrict__ digits, long long dld,
+                                                                long long plane_stride,
+                                                                const int *__restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  const int Pq = (int)(r / nao), mu = (int)(r - (long long)Pq * nao);
+  const int P = perm ? perm[Pq] : Pq;
+  const double *BP = Bp + (long long)P * ((long long)nao * (nao + 1) / 2);
+  const long long row_mu = (long long)mu * nao - (long long)mu * (mu - 1) / 2 - mu;  // + nu for nu >= mu
+  auto at = [&](int nu) -> double {
+    return nu >= mu ? __ldg(BP + row_mu + nu)
+                    : __ldg(BP + (long long)nu * nao - (long long)nu * (nu - 1) / 2 + (mu - nu));
+  };
+  uint64_t m = 0;
+  for (int c = lane; c < nao; c += 32) {
+    const uint64_t a = abs_bits(at(c));
+    m = a > m ? a : m;
+  }
+  m = warp_max_u64(m);
+  const int e = exponent_from_max_bits_dev(m);
+  if (lane == 0) exps[r] = e;
+  uint16_t *drow = digits + r * dld;
+  for (int c = 2 * lane; c < nao; c += 64) {
+    int d0[kSMax], d1[kSMax];
+    balanced_digits(scaled_rne((uint64_t)__double_as_longlong(at(c)), e), d0);
+    const bool two = c + 1 < nao;
+    if (two) {
+      balanced_digits(scaled_rne((uint64_t)__double_as_longlong(at(c + 1)), e), d1);
+    } else {
+#pragma unroll
+      for (int t = 0; t < kSMax; ++t) d1[t] = 0;
+    }
+#pragma unroll
+    for (int t = 0; t < kSMax; ++t) {
+      if (t < nslices) {
+        const uint32_t pk = (uint32_t)int_to_bf16_bits(d0[t]) | ((uint32_t)int_to_bf16_bits(d1[t]) << 16);
+        uint16_t *dst = drow + (long long)t * plane_stride + c;
+        if (two && ((reinterpret_cast<uintptr_t>(dst) & 3) == 0)) {
+          *reinterpret_cast<uint32_t *>(dst) = pk;
+        } else {
+          dst[0] = (uint16_t)(pk & 0xFFFF);
+          if (two) dst[1] = (uint16_t)(pk >> 16);
+        }
+      }
+    }
+  }
+}
+
 // One warp per row, int8 digits [nslices][rows][cols] (inspection entry point).
 __global__ void split_rows_int8_kernel(const double *__restrict__ A, int rows, int cols, int ld, int nslices,
                                        int *__restrict__ exps, int8_t *__restrict__ digits) {
@@ -402,6 +457,15 @@ cudaError_t launch_split_rows_bf16(const double *A, long long rows, int cols, lo
     split_rows_bf16_kernel<32><<<grid, 32 * wpb, 0, st>>>(A, rows, cols, ld, nslices, exps, digits, dld,
                                                          plane_stride, vec2, perm, g);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_rows_packed(const double *Bp, int naux, int nao, int nslices, int *exps, uint16_t *digits,
+                                     long long dld, long long plane_stride, const int *perm, cudaStream_t st) {
+  const long long rows = (long long)naux * nao;
+  if (rows <= 0) return cudaSuccess;
+  split_rows_packed_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(Bp, rows, nao, nslices, exps, digits, dld,
+                                                                        plane_stride, perm);
   return cudaGetLastError();
 }
 

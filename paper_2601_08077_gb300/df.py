@@ -66,6 +66,7 @@ def lib():
         L.df_setup.argtypes = [P, P, V]
         L.df_setup_ordered.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), V]
         L.df_setup_integrals.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_int), V]
+        L.df_setup_packed.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), V]
         L.df_build_J.argtypes = [P, P, P, P, V]
         L.df_build_K.argtypes = [P, P, I, I, P, ctypes.POINTER(KStats), V]
         L.df_build_K_blocks.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(KStats), V]
@@ -280,6 +281,13 @@ class Context:
         else:
             arr = (ctypes.c_int * self.naux)(*[int(x) for x in perm])
             _check(lib().df_setup_ordered(self._h, _f64(B), arr, _stream(stream)), "df_setup_ordered")
+
+    def setup_packed(self, Bp: torch.Tensor, perm=None, stream=None):
+        """Attach B given as packed upper triangles [naux, nao (nao + 1) / 2] (see inputs.pack_upper)."""
+        assert Bp.shape == (self.naux, self.nao * (self.nao + 1) // 2)
+        self._B = Bp
+        arr = None if perm is None else (ctypes.c_int * self.naux)(*[int(x) for x in perm])
+        _check(lib().df_setup_packed(self._h, _f64(Bp), arr, _stream(stream)), "df_setup_packed")
 
     def setup_integrals(self, T: torch.Tensor, V: torch.Tensor, perm=None, stream=None):
         """Form B = L^{-1} T in place on the device (L L^T = V) and attach it; returns T (now B)."""

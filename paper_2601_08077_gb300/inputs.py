@@ -207,6 +207,13 @@ def df_tensor(mol: Molecule, tau: float = 0.0) -> np.ndarray:
     return B
 
 
+def pack_upper(B: np.ndarray) -> np.ndarray:
+    """Each B_P's upper triangle row by row: [naux, nao (nao + 1) / 2] (df_setup_packed's layout)."""
+    naux, nao, _ = B.shape
+    iu = np.triu_indices(nao)
+    return np.ascontiguousarray(B[:, iu[0], iu[1]])
+
+
 def leading_aux(mol: Molecule, nrows: int) -> Molecule:
     """The same molecule with only its first nrows auxiliary functions."""
     if nrows >= mol.naux:
