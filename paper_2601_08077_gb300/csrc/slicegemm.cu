@@ -80,6 +80,7 @@ static_assert(kSmemBytesM <= 232448, "CRT ring must fit the 227 KB opt-in shared
 // to 224; 128*56 + 256*224 = 64512 = 384 threads * 168 registers at launch.
 constexpr int kRegsLow = 56;
 constexpr int kRegsHigh = 224;
+static_assert(128 * kRegsLow + 256 * kRegsHigh <= kThreads * 168, "register split exceeds the launch's registers");
 
 // BF16 x BF16 -> FP32, both operands K-major, M = 128, N = 128 or 256
 // (instruction descriptor of tcgen05.mma .kind::f16: D fmt bits 4-5, A fmt
@@ -495,6 +496,19 @@ __device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m,
 __device__ __forceinline__ int num_chunks(int ktiles) { return (ktiles + kChunkStages - 1) / kChunkStages; }
 __device__ __forceinline__ int chunk_begin(int ktiles, int nch, int c) { return ktiles * c / nch; }
 
+// acc + v 2^sh for 0 <= sh <= 30: one widening multiply-add (2^sh fits a
+// signed 32-bit multiplier), exact in int64
+__device__ __forceinline__ long long mad_pow2(int v, int pow2, long long acc) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(v), "r"(pow2), "l"(acc));
+  return d;
+}
+
+// acc + v 2^sh for 32 <= sh <= 63, modulo 2^64: only the high word changes
+__device__ __forceinline__ long long add_high(int v, int sh_hi, long long acc) {
+  return (long long)((unsigned long long)acc + ((unsigned long long)((uint32_t)v << sh_hi) << 32));
+}
+
 __device__ __forceinline__ long long weigh(int v, int sh) {
   const long long x = (long long)v;
   return sh >= 0 ? (x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
@@ -813,6 +827,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                   }
                 }
+              } else if (two && sh1 >= 0 && sh0 <= 30) {
+                // both weights are powers of two that fit a 32-bit multiplier:
+                // one widening multiply-add per value (the int64 total is exact,
+                // so the sums modulo 2^64 are the sums)
+                const int p0 = 1 << sh0, p1 = 1 << sh1;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                  R[qq * 16 + j] = mad_pow2(__float2int_rz(__uint_as_float(a0[j])), p0, R[qq * 16 + j]);
+                  R[qq * 16 + j] = mad_pow2(__float2int_rz(__uint_as_float(b0[j])), p1, R[qq * 16 + j]);
+                }
+              } else if (two && sh0 >= 32 && sh1 >= 0 && sh1 <= 30) {
+                // the leading pair's weight is 2^32 or more: it adds to the high word
+                const int p1 = 1 << sh1;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                  R[qq * 16 + j] = add_high(__float2int_rz(__uint_as_float(a0[j])), sh0 - 32, R[qq * 16 + j]);
+                  R[qq * 16 + j] = mad_pow2(__float2int_rz(__uint_as_float(b0[j])), p1, R[qq * 16 + j]);
+                }
               } else if (two && sh1 >= 0) {
                 // both weights are non-negative powers of two, 2^8 apart:
                 // v0 2^sh0 + v1 2^sh1 = (v0 2^8 + v1) 2^sh1, exact in int64
@@ -823,6 +855,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                   const long long w2 = ((long long)v0 << 8) + (long long)v1;
                   R[qq * 16 + j] += w2 << sh1;
                 }
+              } else if (!two && sh0 >= 0 && sh0 <= 30) {
+                const int p0 = 1 << sh0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  R[qq * 16 + j] = mad_pow2(__float2int_rz(__uint_as_float(a0[j])), p0, R[qq * 16 + j]);
+              } else if (!two && sh0 >= 32) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  R[qq * 16 + j] = add_high(__float2int_rz(__uint_as_float(a0[j])), sh0 - 32, R[qq * 16 + j]);
               } else if (!two && sh0 >= 0) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
