@@ -272,8 +272,14 @@ const char *df_strerror(df_status s);
  * GEMM, and the reductions (Section 3.3 blocking per molecule, Section 3.2
  * emulation).  With graphs on (the default) the whole sequence is captured
  * once per (nslices, argument pointers) as a CUDA graph and replayed; a NULL
- * stream runs it without a graph.  Pointer arrays are host arrays of device
- * pointers, one per molecule.  The caller keeps the contexts alive. */
+ * stream runs it without a graph.  The per-molecule kernels between the
+ * grouped launches (X splits, reductions; in df_batch_build_J each
+ * molecule's rho and J) run concurrently on four internal streams that fork
+ * from and join back into `stream`, so a call is still ordered with the
+ * caller's other work on `stream`.  Pointer arrays are host arrays of device
+ * pointers, one per molecule.  The contexts must be distinct (DF_ERR_ARG
+ * otherwise: their buffers are written concurrently); the caller keeps them
+ * alive. */
 typedef struct df_batch df_batch;
 df_status df_batch_create(df_batch **out, df_ctx *const *ctxs, int n);
 void df_batch_destroy(df_batch *b);

@@ -37,6 +37,13 @@ struct df_batch {
   std::vector<int> nocc;
   int tables_for_s = -1;
   bool pairs1 = false;  // first GEMM on CTA pairs (swapped layout, tables in tile pairs)
+  // side streams for the per-molecule kernels (X split, reduce, rho and J):
+  // molecule i runs on side[i % kFan] between a fork and a join of the
+  // caller's stream, in eager launches and inside a captured graph alike
+  static constexpr int kFan = 4;
+  cudaStream_t side[kFan] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kFan] = {};
   // graph cache
   cudaGraphExec_t exec_K = nullptr, exec_J = nullptr;
   std::vector<const void *> key_K, key_J;
@@ -50,6 +57,23 @@ df_status cerr(cudaError_t e) { return e == cudaSuccess ? DF_OK : DF_ERR_CUDA; }
 void drop_graph(cudaGraphExec_t &g) {
   if (g) cudaGraphExecDestroy(g);
   g = nullptr;
+}
+
+// The side streams start after everything enqueued on st so far.
+cudaError_t fork(df_batch *b, cudaStream_t st) {
+  cudaError_t e = cudaEventRecord(b->ev_fork, st);
+  for (int k = 0; k < df_batch::kFan && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+  return e;
+}
+
+// st continues after everything enqueued on the side streams so far.
+cudaError_t join(df_batch *b, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < df_batch::kFan && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->ev_join[k], b->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->ev_join[k], 0);
+  }
+  return e;
 }
 
 // Molecule order for the unit lists.
@@ -116,6 +140,7 @@ df_status enqueue_K(df_batch *b, const double *const *C, const int *nocc, int s,
   if (df::launch_slice_gemm_grouped(b->pairs1 ? df::kModeXs : df::kModeX, g1, b->status, 0, st, b->pairs1) !=
       cudaSuccess)
     return DF_ERR_CUDA;
+  if (fork(b, st) != cudaSuccess) return DF_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
     df_ctx *c = b->ctx[i];
     df::ShiftTable t1;
@@ -123,20 +148,23 @@ df_status enqueue_K(df_batch *b, const double *const *C, const int *nocc, int s,
     for (int q = 0; q <= 8; ++q) t1.v[q] = df::fixed_point_shift(q, k1);
     if (df::launch_split_xblocks(reinterpret_cast<const long long *>(c->X), c->naux, c->nao, nocc[i], s, c->eB,
                                  c->eC, c->sblk, t1, c->eX, c->Xd, df::xdigit_ld(nocc[i]), c->nblk,
-                                 st) != cudaSuccess)
+                                 b->side[i % df_batch::kFan]) != cudaSuccess)
       return DF_ERR_CUDA;
   }
+  if (join(b, st) != cudaSuccess) return DF_ERR_CUDA;
   df::SgGroup g2{b->params2, b->maps2, b->off2, n, b->total2};
   if (df::launch_slice_gemm_grouped(df::kModeKPart, g2, b->status, 0, st) != cudaSuccess) return DF_ERR_CUDA;
+  if (fork(b, st) != cudaSuccess) return DF_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
     df_ctx *c = b->ctx[i];
     df::ShiftTable tt;
     const long long kb = df::xdigit_ld(nocc[i]);
     for (int q = 0; q <= 8; ++q) tt.v[q] = df::fixed_point_shift(q, kb);
-    if (df::launch_kpart_reduce(c->Rp, c->eX, c->sblk, tt, c->nao, c->nblk, b->nsplit[i], K[i], st) != cudaSuccess)
+    if (df::launch_kpart_reduce(c->Rp, c->eX, c->sblk, tt, c->nao, c->nblk, b->nsplit[i], K[i],
+                                b->side[i % df_batch::kFan]) != cudaSuccess)
       return DF_ERR_CUDA;
   }
-  return DF_OK;
+  return join(b, st) == cudaSuccess ? DF_OK : DF_ERR_CUDA;
 }
 
 df_status prepare(df_batch *b, const int *nocc, int s, cudaStream_t st) {
@@ -169,8 +197,25 @@ df_status df_batch_create(df_batch **out, df_ctx *const *ctxs, int n) {
   *out = nullptr;
   df_batch *b = new (std::nothrow) df_batch();
   if (!b) return DF_ERR_OOM;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) {
+      delete b;
+      return DF_ERR_ARG;
+    }
+    // each molecule needs its own context: their kernels run concurrently
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) {
+        delete b;
+        return DF_ERR_ARG;
+      }
+  }
   b->ctx.assign(ctxs, ctxs + n);
-  cudaError_t e = cudaMalloc(&b->params1, sizeof(df::SgParams) * n);
+  cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < df_batch::kFan && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->params1, sizeof(df::SgParams) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->params2, sizeof(df::SgParams) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->maps1, sizeof(CUtensorMap) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->maps2, sizeof(CUtensorMap) * 2 * n);
@@ -190,6 +235,11 @@ void df_batch_destroy(df_batch *b) {
   if (!b) return;
   drop_graph(b->exec_K);
   drop_graph(b->exec_J);
+  for (int k = 0; k < df_batch::kFan; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   cudaFree(b->params1);
   cudaFree(b->params2);
   cudaFree(b->maps1);
@@ -243,16 +293,19 @@ df_status df_batch_build_J(df_batch *b, const double *const *D, double *const *J
   if (!b || !D || !J) return DF_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int n = (int)b->ctx.size();
+  for (int i = 0; i < n; ++i)
+    if (!b->ctx[i]->ready) return DF_ERR_STATE;
   auto enqueue = [&]() -> df_status {
+    if (fork(b, st) != cudaSuccess) return DF_ERR_CUDA;
     for (int i = 0; i < n; ++i) {
       df_ctx *c = b->ctx[i];
-      if (!c->ready) return DF_ERR_STATE;
+      cudaStream_t si = b->side[i % df_batch::kFan];
       const uint32_t *mk = df::use_mask_mu(c);
-      if (df::launch_rho(c->B, D[i], c->naux, c->nao, c->rho, st, mk, c->packed) != cudaSuccess) return DF_ERR_CUDA;
-      if (df::launch_coulomb(c->B, c->rho, c->naux, c->nao, J[i], st, mk, c->packed) != cudaSuccess)
+      if (df::launch_rho(c->B, D[i], c->naux, c->nao, c->rho, si, mk, c->packed) != cudaSuccess) return DF_ERR_CUDA;
+      if (df::launch_coulomb(c->B, c->rho, c->naux, c->nao, J[i], si, mk, c->packed) != cudaSuccess)
         return DF_ERR_CUDA;
     }
-    return DF_OK;
+    return join(b, st) == cudaSuccess ? DF_OK : DF_ERR_CUDA;
   };
   if (!b->graphs || st == nullptr) return enqueue();
   std::vector<const void *> key;

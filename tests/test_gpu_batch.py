@@ -101,3 +101,45 @@ def test_autotuner_choice_depends_on_the_molecule_mix(df):
             assert torch.equal(k, k1)
     print("autotuner choices (K-split cap, order, first-GEMM tile):", chosen)
     assert chosen["one-large-nocc"][2] == 0 and chosen["small-nocc"][2] in (0, 1)
+
+
+def test_batch_side_streams_join_the_callers_stream(df, molecules):
+    """Six molecules over the four side streams (two streams carry two molecules), with and
+    without graphs: copies enqueued on the caller's stream right after a build see every
+    molecule's finished K and J; a batch that names one context twice is refused."""
+    s = 4
+    mols = list(molecules)
+    for atoms, seed in [(16, 21), (27, 22)]:
+        mol = inputs.molecule(atoms, seed)
+        C = inputs.orbitals(mol.nao, atoms, seed + 1)
+        mols.append((inputs.df_tensor(mol), C, inputs.density(C)))
+    ctxs, keep = [], []
+    for B, C, D in mols:
+        ctx = df.Context(B.shape[1], B.shape[0], C.shape[1], s_max=s)
+        Bg = torch.from_numpy(B).cuda()
+        ctx.setup(Bg)
+        ctxs.append(ctx)
+        keep.append(Bg)
+    Cs = [torch.from_numpy(C).cuda() for _, C, _ in mols]
+    Ds = [torch.from_numpy(D).cuda() for _, _, D in mols]
+    single = [ctx.build_K(C, s)[0].clone() for ctx, C in zip(ctxs, Cs)]
+    Js1 = [ctx.build_J(D)[0].clone() for ctx, D in zip(ctxs, Ds)]
+    with pytest.raises(RuntimeError):
+        df.Batch([ctxs[0], ctxs[1], ctxs[0]])
+    batch = df.Batch(ctxs)
+    stream = torch.cuda.Stream()
+    for graphs in (True, False):
+        batch.set_graphs(graphs)
+        Ks = [torch.full_like(k, float("nan")) for k in single]
+        Js = [torch.full_like(j, float("nan")) for j in Js1]
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                batch.build_K(Cs, s, Ks, stream=stream)
+                Kc = [k.clone() for k in Ks]
+                batch.build_J(Ds, Js, stream=stream)
+                Jc = [j.clone() for j in Js]
+        stream.synchronize()
+        for k, k1 in zip(Kc, single):
+            assert torch.equal(k, k1)
+        for j, j1 in zip(Jc, Js1):
+            assert torch.equal(j, j1)
