@@ -136,6 +136,10 @@ df_status enqueue_K(df_batch *b, const double *const *C, const int *nocc, int s,
     if (df::launch_split_cols_bf16(C[i], c->nao, nocc[i], s, c->eC, c->Cd, c->ld_nao, c_plane, st) != cudaSuccess)
       return DF_ERR_CUDA;
   }
+  for (int i = 0; i < n; ++i)
+    if (cudaMemsetAsync(b->ctx[i]->rowE, 0x80, sizeof(int) * (size_t)b->ctx[i]->nblk * b->ctx[i]->nao, st) !=
+        cudaSuccess)
+      return DF_ERR_CUDA;
   df::SgGroup g1{b->params1, b->maps1, b->off1, n, b->total1};
   if (df::launch_slice_gemm_grouped(b->pairs1 ? df::kModeXs : df::kModeX, g1, b->status, 0, st, b->pairs1) !=
       cudaSuccess)
@@ -147,7 +151,7 @@ df_status enqueue_K(df_batch *b, const double *const *C, const int *nocc, int s,
     const long long k1 = (long long)((c->nao + df::kKTile - 1) / df::kKTile) * df::kKTile;
     for (int q = 0; q <= 8; ++q) t1.v[q] = df::fixed_point_shift(q, k1);
     if (df::launch_split_xblocks(reinterpret_cast<const long long *>(c->X), c->naux, c->nao, nocc[i], s, c->eB,
-                                 c->eC, c->sblk, t1, c->eX, c->Xd, df::xdigit_ld(nocc[i]), c->nblk,
+                                 c->eC, c->sblk, t1, c->rowE, c->eX, c->Xd, df::xdigit_ld(nocc[i]), c->nblk,
                                  b->side[i % df_batch::kFan]) != cudaSuccess)
       return DF_ERR_CUDA;
   }

@@ -190,6 +190,7 @@ bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap 
     p.status = c->status;
     p.pair = c->pair_mode;
     p.kmask = use_mask_tile(c);
+    p.rowE = c->rowE;
     return true;
   }
   if (!make_tmap_bf16(&ta, c->Cd, nao, nocc, c->s_max, c->ld_nao, c_plane)) return false;
@@ -217,6 +218,7 @@ bool gemm1_setup(df_ctx *c, int nocc, SgParams &p, CUtensorMap &ta, CUtensorMap 
   p.status = c->status;
   p.pair = c->pair_mode;
   p.kmask = use_mask_tile(c);
+  p.rowE = c->rowE;
   return true;
 }
 
@@ -276,6 +278,7 @@ df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_pla
   df::SgParams p;
   CUtensorMap ta, tb;
   if (!df::gemm1_setup(c, nocc, p, ta, tb)) return record(c, DF_ERR_CUDA);
+  DF_TRY(c, cudaMemsetAsync(c->rowE, 0x80, sizeof(int) * (size_t)c->nblk * nao, st));
   {
     PhaseTimer t(c, DF_PHASE_GEMM1, st);
     DF_TRY(c, df::launch_slice_gemm(p, ta, tb, st));
@@ -287,7 +290,7 @@ df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_pla
     df::ShiftTable t1;
     for (int q = 0; q <= 8; ++q) t1.v[q] = p.shiftT[q];
     DF_TRY(c, df::launch_split_xblocks(reinterpret_cast<const long long *>(c->X), naux, nao, nocc, smax, c->eB,
-                                       c->eC, c->sblk, t1, c->eX, c->Xd, kb_ld, c->nblk, st));
+                                       c->eC, c->sblk, t1, c->rowE, c->eX, c->Xd, kb_ld, c->nblk, st));
   }
   return DF_OK;
 }
@@ -399,6 +402,7 @@ df_status df_create(df_ctx **out, int nao, int naux, int nocc_max, int s_max) {
   if (e == cudaSuccess) e = alloc(c, &c->X, (size_t)rowsB * nocc_max);
   if (e == cudaSuccess) e = alloc(c, &c->Xd, (size_t)s_max * c->nblk * nao * c->kb_ld_max);
   if (e == cudaSuccess) e = alloc(c, &c->eX, (size_t)c->nblk * nao);
+  if (e == cudaSuccess) e = alloc(c, &c->rowE, (size_t)c->nblk * nao);
   {
     // split the K range of each block so that the second GEMM's units fill
     // whole waves of the persistent grid: the smallest split (fewest partials)
@@ -460,6 +464,7 @@ void df_destroy(df_ctx *c) {
   cudaFree(c->X);
   cudaFree(c->Xd);
   cudaFree(c->eX);
+  cudaFree(c->rowE);
   cudaFree(c->Rp);
   cudaFree(c->rho);
   cudaFree(c->epart);

@@ -19,6 +19,7 @@ struct df_ctx {
   double *X = nullptr;  // emulated path: the first GEMM's int64 sums (same size); FP64 path: X^T
   uint16_t *Xd = nullptr;
   int *eX = nullptr;
+  int *rowE = nullptr;      // [nblk][nao] the first GEMM's bound on each X row's exponent
   long long *Rp = nullptr;  // int64 partials of the second GEMM [nblk][nsplit][nao][nao]
   int nsplit = 1;
   double *rho = nullptr;

@@ -77,7 +77,17 @@ struct SgParams {
   // B's (P, mu) rows, the bit mask of its nonzero 64-wide K tiles (bit k = K
   // tile k, at most 32); null = dense
   const uint32_t *kmask;
+  // first exchange GEMM (kModeX / kModeXs): per (block, mu) row of X, the
+  // largest bit-length bound E = bitlen(|R|) + k over the row's nonzero exact
+  // sums R (|R 2^k| < 2^E), atomically maxed; the X split takes it as its
+  // exponent guess and so reads R once.  Reset to kRowBoundNone before the
+  // launch; null = not recorded.
+  int *rowE;
 };
+
+// "No nonzero element yet" in a row bound (the byte 0x80 repeated, so a
+// memset resets it); below every real bound.
+constexpr int kRowBoundNone = (int)0x80808080;
 
 // Tile pairs of a launch in CTA-pair mode (0 = the layout has no pairing):
 // kLayoutGrid / kLayoutX pair m tiles 2a, 2a+1 of one n tile (nt_m even);
@@ -129,10 +139,11 @@ struct ShiftTable {
 };
 // R: the first GEMM's int64 sums (kModeX); X = fl64(R 2^k) is formed here with
 // the first GEMM's exponents eB (rows (P, mu)), eC (orbitals), slices s_blk and
-// truncation table T1, then split per (block, mu).
+// truncation table T1, then split per (block, mu).  rowE: the first GEMM's
+// per-row bound (SgParams::rowE) when it recorded one, else null.
 cudaError_t launch_split_xblocks(const long long *R, int naux, int nao, int nocc, int nslices, const int *eB,
-                                 const int *eC, const int *s_blk, const ShiftTable &T1, int *eX, uint16_t *Xd,
-                                 long long kb_ld, int nblk, cudaStream_t st);
+                                 const int *eC, const int *s_blk, const ShiftTable &T1, const int *rowE, int *eX,
+                                 uint16_t *Xd, long long kb_ld, int nblk, cudaStream_t st);
 cudaError_t launch_kpart_reduce(const long long *Rp, const int *eX, const int *s_blk, ShiftTable T, int nao,
                                 int nblk, int nsplit, double *K, cudaStream_t st);
 

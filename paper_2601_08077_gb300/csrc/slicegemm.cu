@@ -437,6 +437,74 @@ __device__ __forceinline__ int mod_i40(long long R, int m, uint32_t magic, int c
   return r >= m ? r - m : r;
 }
 
+// First exchange GEMM: this unit's part of the per-(block, mu) bound on the
+// exponent of each X row (SgParams::rowE).  An element's exact sum R with
+// exponent sum k has |R 2^k| < 2^E, E = bitlen(|R|) + k, two integer
+// operations with no rounding; the row bound is the largest E of its nonzero
+// elements.  kModeX: a thread's 64 columns are 64 (P, mu) rows of X and the
+// lanes of its warp are orbitals, so each column is maxed over the warp with
+// one redux and one lane adds it atomically; kModeXs: the thread's row is one
+// (P, mu), its columns orbitals, so it maxes its own values.  Lanes that gave
+// up on a wait are not here; the reduction takes the lanes that are.
+__device__ __forceinline__ int bit_length(long long r) {
+  const uint64_t u = r < 0 ? (uint64_t)(-(r + 1)) + 1ull : (uint64_t)r;
+  return 64 - __clzll((long long)u);
+}
+
+template <int kMode>
+__device__ __forceinline__ void record_row_bound(const SgParams &p, int m, int n0c, const long long (&R)[64],
+                                                 int kexp_base, int lane) {
+  if constexpr (kMode == kModeX) {
+    // v[j]: this lane's bound for column j without the column's exponent
+    // eb[n] (the same on every lane, added by the lane that ends up owning the
+    // column).  A butterfly reduce-scatter over the warp: at each of five steps
+    // a lane keeps half of its columns, sends the other half to its partner
+    // and maxes what it receives; the shuffles of a step are independent, and
+    // lane L ends with columns 2L and 2L + 1.
+    const unsigned active = __activemask();
+    const bool mv = m < p.m_valid;
+    const int km = kexp_base + (mv ? p.ea[m] : 0);
+    int v[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j)
+      v[j] = (mv && n0c + j < p.n_valid && R[j] != 0) ? bit_length(R[j]) + km : kRowBoundNone;
+#pragma unroll
+    for (int w = 32; w >= 2; w >>= 1) {
+      // w columns held; keep w / 2: the upper half when this lane's bit is set
+      const int bit = (w == 32 ? 16 : w == 16 ? 8 : w == 8 ? 4 : w == 4 ? 2 : 1);
+      const bool upper = (lane & bit) != 0;
+#pragma unroll
+      for (int i = 0; i < w; ++i) {
+        const int send = upper ? v[i] : v[i + w];
+        const int keep = upper ? v[i + w] : v[i];
+        const int got = __shfl_xor_sync(active, send, bit);
+        v[i] = keep > got ? keep : got;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int n = n0c + 2 * lane + h;
+      if (v[h] != kRowBoundNone && n < p.n_valid) {
+        const int P = n / p.nao, mu = n - P * p.nao;
+        atomicMax(p.rowE + (P / kBlock) * p.nao + mu, v[h] + __ldg(p.eb + n));
+      }
+    }
+  } else if constexpr (kMode == kModeXs) {
+    if (m >= p.m_valid) return;
+    const int km = kexp_base + p.ea[m];
+    int best = kRowBoundNone;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      const int n = n0c + j;
+      if (n < p.n_valid && R[j] != 0) best = max(best, bit_length(R[j]) + km + __ldg(p.eb + n));
+    }
+    if (best != kRowBoundNone) {
+      const int P = m / p.nao, mu = m - P * p.nao;
+      atomicMax(p.rowE + (P / kBlock) * p.nao + mu, best);
+    }
+  }
+}
+
 template <int kMode>
 __device__ __forceinline__ void store64(const SgParams &p, const Unit &w, int m, int n0c, const long long (&R)[64],
                                         int kexp_base, int ea_m) {
@@ -886,6 +954,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (ok && kMode != kModeRaw) store64<kMode>(q, w, m, n_base, R, kexp_base, ea_m);
+      if constexpr (kMode == kModeX || kMode == kModeXs) {
+        if (ok && q.rowE) record_row_bound<kMode>(q, m, n_base, R, kexp_base, lane);
+      }
     }
   }
 

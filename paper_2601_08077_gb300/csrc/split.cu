@@ -9,10 +9,10 @@
 // All of it is integer arithmetic on the FP64 bit patterns.  The digits feed
 // the tensor cores as BF16 (every integer in [-256, 256] is exact in BF16).
 // These kernels are HBM-bound: each reads its FP64 input and writes s
-// digits per value, in two passes over a row (its maximum, then the digits).
-// For the B and C splits the second pass mostly hits L1/L2; the X split's
-// rows (128 functions x nocc values, up to 256 KB) are mostly re-read from
-// DRAM.
+// digits per value, in two passes over a row (its maximum, then the digits);
+// for the B and C splits the second pass mostly hits L1/L2.  The X split's
+// rows (128 functions x nocc values, up to 256 KB) take their exponent bound
+// from the first GEMM and are read once.
 #include "df_internal.h"
 
 #include <climits>
@@ -227,11 +227,16 @@ __global__ void split_cols_bf16_kernel(const double *__restrict__ C, int nrows, 
 // X = fl64(R 2^k), k = -14 - 8(s_b - 1) + T(s_b) + eC[i] + eB[(P, mu)], the
 // one rounding of the emulated product, and splits it.  (Doing the rounding
 // here keeps the GEMM's epilogue short; it measured 18% faster that way.)
-// The first pass finds the row's largest |X| from exact magnitude keys, the
-// second re-reads the row (256 KB at most, mostly from DRAM) and writes the
-// digits.  Two consecutive orbitals per thread (16-byte loads, 4-byte stores)
-// when nocc is even, four loads in flight per thread in the first pass.
+// The row's exponent needs its largest |X| (exact magnitude keys).  When the
+// first GEMM recorded its bound E for the row (rowE), the exponent is E or
+// E + 1, so one pass writes the digits with E while it takes the keys, and
+// only a row whose exact exponent differs (about one in a hundred) is read
+// a second time; R is read once.  Without the bound, a first pass takes the
+// keys and a second re-reads the row (256 KB at most, mostly from DRAM) for
+// the digits.  Two consecutive orbitals per thread (16-byte loads, 4-byte
+// stores) when nocc is even.
 constexpr int kSplitXThreads = 256;
+constexpr int kSplitXMinBlocks = 6;  // 40 registers: six rows in flight per SM (four at 51 measured slower)
 constexpr int kP1 = 4;  // loads in flight per thread in the first pass (8 measured slower)
 
 // Digit t of the balanced expansion of N as an exact FP32 value, from
@@ -256,8 +261,9 @@ struct XScale {
   ShiftTable T;         // truncation of the first GEMM's fixed-point sum, by s
 };
 
-__global__ void __launch_bounds__(kSplitXThreads) split_xblocks_kernel(const long long *__restrict__ R, int naux,
+__global__ void __launch_bounds__(kSplitXThreads, kSplitXMinBlocks) split_xblocks_kernel(const long long *__restrict__ R, int naux,
                                                                        int nao, int nocc, int nslices, XScale xs,
+                                                                       const int *__restrict__ rowE,
                                                                        int *__restrict__ eX,
                                                                        uint16_t *__restrict__ Xd, long long kb_ld,
                                                                        int nblk) {
@@ -280,54 +286,93 @@ __global__ void __launch_bounds__(kSplitXThreads) split_xblocks_kernel(const lon
     for (int q = threadIdx.x; q < nocc; q += blockDim.x) eI[q] = xs.eC[q];
   }
   __syncthreads();
-  {
-    // largest magnitude key (E, M) of the row; E = INT_MIN marks "none yet"
-    int bE = INT_MIN;
-    uint64_t bM = 0;
-    auto take = [&](long long r, int k) {
-      if (r == 0) return;
-      int E;
-      uint64_t M;
-      mag_key(r, k, E, M);
-      if (E > bE || (E == bE && M > bM)) {
-        bE = E;
-        bM = M;
-      }
-    };
+  const long long plane = (long long)nblk * nao * kb_ld;
+  uint16_t *dst = Xd + ((long long)b * nao + mu) * kb_ld;
+  const long long *row0 = R + ((long long)p0 * nao + mu) * nocc;  // element (pl, i) at row0[pl nao nocc + i]
+  const long long pstride = (long long)nao * nocc;
+
+  // largest magnitude key (E, M) of the row seen by this thread; E = INT_MIN marks "none yet"
+  int bE = INT_MIN;
+  uint64_t bM = 0;
+  auto take = [&](long long r, int k) {
+    if (r == 0) return;
+    int E;
+    uint64_t M;
+    mag_key(r, k, E, M);
+    if (E > bE || (E == bE && M > bM)) {
+      bE = E;
+      bM = M;
+    }
+  };
+
+  // The digits of the whole row (zero digits in the padding) with exponent e;
+  // with keys, the magnitude keys of the row's elements are taken on the way.
+  auto digits_pass = [&](int e, bool keys) {
     if ((nocc & 1) == 0) {
       const int hp = nocc >> 1;
-      const int total = nP * hp;
-      for (int q0 = threadIdx.x; q0 < total; q0 += kP1 * blockDim.x) {
-        longlong2 v[kP1];
-        int kp[kP1], ki[kP1];
+      constexpr long long kBias = 0x0080808080808080ll;  // 128 in each of the seven low bytes
+      constexpr int kU = 2;                                // pairs per thread per iteration (4 measured slower)
+      for (int q0 = threadIdx.x; 2 * q0 < kpad; q0 += kU * blockDim.x) {
+        longlong2 v[kU];
+        int kq[kU];
 #pragma unroll
-        for (int r = 0; r < kP1; ++r) {
+        for (int r = 0; r < kU; ++r) {
           const int q = q0 + r * blockDim.x;
-          if (q < total) {
+          const int k = 2 * q;
+          v[r] = make_longlong2(0, 0);  // N = 0 (padding) gives zero digits
+          kq[r] = -1;
+          if (k < klen) {
             const int pl = q / hp;
-            const int i = 2 * (q - pl * hp);
-            v[r] = *reinterpret_cast<const longlong2 *>(R + ((long long)(p0 + pl) * nao + mu) * nocc + i);
-            kp[r] = eP[pl];
-            ki[r] = i;
-          } else {
-            v[r] = make_longlong2(0, 0);
-            kp[r] = 0;
-            ki[r] = 0;
+            const int i = k - pl * nocc;
+            v[r] = *reinterpret_cast<const longlong2 *>(row0 + pl * pstride + i);
+            kq[r] = pl;
           }
         }
 #pragma unroll
-        for (int r = 0; r < kP1; ++r) {
-          take(v[r].x, kp[r] + eI[ki[r]]);
-          take(v[r].y, kp[r] + eI[ki[r] + 1]);
+        for (int r = 0; r < kU; ++r) {
+          const int q = q0 + r * blockDim.x;
+          const int k = 2 * q;
+          if (k >= kpad) continue;
+          long long M0 = kBias, M1 = kBias;
+          if (kq[r] >= 0) {
+            const int i = k - kq[r] * nocc;
+            const int kp = eP[kq[r]];
+            if (keys) {
+              take(v[r].x, kp + eI[i]);
+              take(v[r].y, kp + eI[i + 1]);
+            }
+            M0 += scaled_rne_i64(v[r].x, kp + eI[i], e);
+            M1 += scaled_rne_i64(v[r].y, kp + eI[i + 1], e);
+          }
+#pragma unroll
+          for (int t = 0; t < kSMax; ++t)
+            if (t < nslices)
+              *reinterpret_cast<uint32_t *>(dst + (long long)t * plane + k) =
+                  bf16x2_of(digit_f32(M0, t), digit_f32(M1, t));
         }
       }
     } else {
-      for (int k = threadIdx.x; k < klen; k += blockDim.x) {
-        const int pl = k / nocc;
-        const int i = k - pl * nocc;
-        take(R[((long long)(p0 + pl) * nao + mu) * nocc + i], eP[pl] + eI[i]);
+      for (int k = threadIdx.x; k < kpad; k += blockDim.x) {
+        int d[kSMax];
+        if (k < klen) {
+          const int pl = k / nocc;
+          const int i = k - pl * nocc;
+          const long long r = row0[pl * pstride + i];
+          if (keys) take(r, eP[pl] + eI[i]);
+          balanced_digits(scaled_rne_i64(r, eP[pl] + eI[i], e), d);
+        } else {
+#pragma unroll
+          for (int t = 0; t < kSMax; ++t) d[t] = 0;
+        }
+#pragma unroll
+        for (int t = 0; t < kSMax; ++t)
+          if (t < nslices) dst[(long long)t * plane + k] = int_to_bf16_bits(d[t]);
       }
     }
+  };
+
+  // The row's exponent from the keys of all threads: e_sh (every thread reads it after the barrier).
+  auto reduce_keys = [&]() {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const int E2 = __shfl_xor_sync(0xffffffffu, bE, o);
@@ -354,64 +399,56 @@ __global__ void __launch_bounds__(kSplitXThreads) split_xblocks_kernel(const lon
       eX[b * nao + mu] = e_sh;
     }
     __syncthreads();
-  }
-  const int e = e_sh;
-  const long long plane = (long long)nblk * nao * kb_ld;
-  uint16_t *dst = Xd + ((long long)b * nao + mu) * kb_ld;
-  if ((nocc & 1) == 0) {
-    const int hp = nocc >> 1;
-    constexpr long long kBias = 0x0080808080808080ll;  // 128 in each of the seven low bytes
-    constexpr int kU = 2;                                // pairs per thread per iteration (loads in flight; 4 measured slower)
-    for (int q0 = threadIdx.x; 2 * q0 < kpad; q0 += kU * blockDim.x) {
-      longlong2 v[kU];
-      int kq[kU];
-#pragma unroll
-      for (int r = 0; r < kU; ++r) {
-        const int q = q0 + r * blockDim.x;
-        const int k = 2 * q;
-        v[r] = make_longlong2(0, 0);  // N = 0 (padding) gives zero digits
-        kq[r] = -1;
-        if (k < klen) {
-          const int pl = q / hp;
-          const int i = k - pl * nocc;
-          v[r] = *reinterpret_cast<const longlong2 *>(R + ((long long)(p0 + pl) * nao + mu) * nocc + i);
-          kq[r] = pl;
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < kU; ++r) {
-        const int q = q0 + r * blockDim.x;
-        const int k = 2 * q;
-        if (k >= kpad) continue;
-        long long M0 = kBias, M1 = kBias;
-        if (kq[r] >= 0) {
-          const int i = k - kq[r] * nocc;
-          const int kp = eP[kq[r]];
-          M0 += scaled_rne_i64(v[r].x, kp + eI[i], e);
-          M1 += scaled_rne_i64(v[r].y, kp + eI[i + 1], e);
-        }
-#pragma unroll
-        for (int t = 0; t < kSMax; ++t)
-          if (t < nslices)
-            *reinterpret_cast<uint32_t *>(dst + (long long)t * plane + k) =
-                bf16x2_of(digit_f32(M0, t), digit_f32(M1, t));
-      }
-    }
+  };
+
+  if (rowE) {
+    // One read of R: the row's largest |X| lies in [2^(E-1), 2^E] for the first
+    // GEMM's bound E, so its exponent is E, or E + 1 when it reaches 127/128 2^E
+    // (or an all-zero row after rounding): digits with the guess, keys on the
+    // way, and a second pass only for a row whose exponent differs.
+    const int g = __ldg(rowE + b * nao + mu);
+    const int e0 = g == kRowBoundNone ? exponent_from_max_bits_dev(0ull) : g;
+    digits_pass(e0, true);
+    reduce_keys();
+    if (e_sh != e0) digits_pass(e_sh, false);
   } else {
-    for (int k = threadIdx.x; k < kpad; k += blockDim.x) {
-      int d[kSMax];
-      if (k < klen) {
+    // two passes: the keys (four loads in flight per thread), then the digits
+    if ((nocc & 1) == 0) {
+      const int hp = nocc >> 1;
+      const int total = nP * hp;
+      for (int q0 = threadIdx.x; q0 < total; q0 += kP1 * blockDim.x) {
+        longlong2 v[kP1];
+        int kp[kP1], ki[kP1];
+#pragma unroll
+        for (int r = 0; r < kP1; ++r) {
+          const int q = q0 + r * blockDim.x;
+          if (q < total) {
+            const int pl = q / hp;
+            const int i = 2 * (q - pl * hp);
+            v[r] = *reinterpret_cast<const longlong2 *>(row0 + pl * pstride + i);
+            kp[r] = eP[pl];
+            ki[r] = i;
+          } else {
+            v[r] = make_longlong2(0, 0);
+            kp[r] = 0;
+            ki[r] = 0;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kP1; ++r) {
+          take(v[r].x, kp[r] + eI[ki[r]]);
+          take(v[r].y, kp[r] + eI[ki[r] + 1]);
+        }
+      }
+    } else {
+      for (int k = threadIdx.x; k < klen; k += blockDim.x) {
         const int pl = k / nocc;
         const int i = k - pl * nocc;
-        balanced_digits(scaled_rne_i64(R[((long long)(p0 + pl) * nao + mu) * nocc + i], eP[pl] + eI[i], e), d);
-      } else {
-#pragma unroll
-        for (int t = 0; t < kSMax; ++t) d[t] = 0;
+        take(row0[pl * pstride + i], eP[pl] + eI[i]);
       }
-#pragma unroll
-      for (int t = 0; t < kSMax; ++t)
-        if (t < nslices) dst[(long long)t * plane + k] = int_to_bf16_bits(d[t]);
     }
+    reduce_keys();
+    digits_pass(e_sh, false);
   }
 }
 
@@ -485,7 +522,7 @@ cudaError_t launch_split_cols_bf16(const double *C, int nrows, int ncols, int ns
 }
 
 cudaError_t launch_split_xblocks(const long long *R, int naux, int nao, int nocc, int nslices, const int *eB,
-                                 const int *eC, const int *s_blk, const ShiftTable &T1,
+                                 const int *eC, const int *s_blk, const ShiftTable &T1, const int *rowE,
                                  int *eX, uint16_t *Xd, long long kb_ld, int nblk, cudaStream_t st) {
   const size_t sm = sizeof(int) * (size_t)(kBlock + nocc);
   static size_t attr = 48 * 1024;
@@ -496,7 +533,8 @@ cudaError_t launch_split_xblocks(const long long *R, int naux, int nao, int nocc
   }
   XScale xs{eB, eC, s_blk, T1};
   dim3 grid(nao, nblk);
-  split_xblocks_kernel<<<grid, kSplitXThreads, sm, st>>>(R, naux, nao, nocc, nslices, xs, eX, Xd, kb_ld, nblk);
+  split_xblocks_kernel<<<grid, kSplitXThreads, sm, st>>>(R, naux, nao, nocc, nslices, xs, rowE, eX, Xd, kb_ld,
+                                                         nblk);
   return cudaGetLastError();
 }
 
