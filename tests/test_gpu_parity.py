@@ -367,8 +367,9 @@ def test_cluster_pairs_option_is_checked(df, small):
 
 def test_exchange_zero_rows(df, small):
     # AO functions 0 and 7 removed from B: the rows (block, mu) of X for them
-    # are zero in every block, so the X split takes its full-scan path there
-    # (exponent 0, zero digits) and K's rows and columns 0 and 7 are zero
+    # are zero in every block, so the first GEMM records no exponent bound for
+    # them, the X split takes exponent 0 and zero digits, and K's rows and
+    # columns 0 and 7 are zero
     B, C, D = small
     B = B.copy()
     for mu in (0, 7):
@@ -379,6 +380,36 @@ def test_exchange_zero_rows(df, small):
         K = ctx.build_K(cuda(C), s)[0].cpu().numpy()
         assert np.array_equal(K, O.emulated_exchange(B, C, s))
         assert not K[[0, 7]].any() and not K[:, [0, 7]].any()
+
+
+@pytest.mark.parametrize("pairs", [1, 0])
+@pytest.mark.parametrize("nocc", [15, 16])
+def test_x_split_rows_above_their_bound(df, pairs, nocc):
+    """Rows of X whose largest |X| reaches 127/128 2^E for the first GEMM's bound E: their
+    exponent is E + 1, so the X split reads them a second time.  With C's columns the unit
+    vectors e_i, X[P, mu, i] = B[P, mu, i] (digit-truncated); a planted |B| = 0.999 above
+    |B| < 0.5 everywhere else puts every other mu row of each block at exponent 1 against a bound
+    of 0.  Both first-GEMM layouts (bound per thread with pairs, per warp without), odd and even
+    nocc; K bit-exact against the oracle's emulation."""
+    rng = np.random.default_rng(300 + nocc)
+    nao, naux = 64, 192
+    B = rng.uniform(-0.5, 0.5, (naux, nao, nao))
+    B = 0.5 * (B + B.transpose(0, 2, 1))
+    for b0 in (0, 128):
+        for mu in range(0, nao, 2):
+            P, i = b0 + 5 + (mu % 7), mu % nocc
+            v = 0.999 if (mu // 2) % 2 == 0 else -0.999
+            B[P, mu, i] = B[P, i, mu] = v
+    C = np.zeros((nao, nocc))
+    C[np.arange(nocc), np.arange(nocc)] = 1.0
+    ctx = df.Context(nao, naux, nocc)
+    ctx.set_cluster_pairs(pairs)
+    Bg = cuda(B)
+    ctx.setup(Bg)
+    for s in (3, 5):
+        K = ctx.build_K(cuda(C), s)[0].cpu().numpy()
+        assert np.array_equal(K, O.emulated_exchange(B, C, s))
+    ctx.sync_status()
 
 
 @pytest.mark.parametrize("nocc", [19, 20])
