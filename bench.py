@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--aux-blocks", type=int, default=0,
                     help="keep only the first N 128-function auxiliary blocks of the workload (a smaller case of "
                          "the same kernels, for profiling); 0 keeps them all")
+    ap.add_argument("--jk-overlap", type=int, choices=[0, 1, 2, 3, 4], default=4,
+                    help="CTAs per SM of rho and J beside the X split in the J + K build (df_build_JK); "
+                         "0 runs J, then K, in one stream")
     ap.add_argument("--cluster-pairs", type=int, choices=[0, 1, 2], default=1,
                     help="slice GEMMs on CTA pairs (cta_group::2): 0 never, 1 the first GEMM, 2 both GEMMs")
     return ap.parse_args()
@@ -629,6 +632,7 @@ def main():
     Dg = torch.from_numpy(D).to(dev)
     B_bytes = Bg.numel() * 8
     ctx.set_cluster_pairs(args.cluster_pairs)
+    ctx.set_jk_overlap(args.jk_overlap)
     J = torch.empty((w.nao, w.nao), dtype=torch.float64, device=dev)
     K = torch.empty_like(J)
     rho = torch.empty(w.naux, dtype=torch.float64, device=dev)
@@ -648,8 +652,7 @@ def main():
     del Ks, K64
 
     def step():
-        ctx.build_J(Dg, J, rho)
-        ctx.build_K(Cg, s, K)
+        ctx.build_JK(Dg, Cg, s, J, rho, K)
         ctx.energy(Dg, J, K, rho)
 
     for _ in range(args.warmup):
@@ -670,6 +673,8 @@ def main():
         torch.cuda.synchronize()
     ctx.set_profiling(False)
     phases = ctx.phase_times()
+    # the one-call build returns the separate builds' J and K bit for bit
+    jk_same = bool(np.array_equal(J.cpu().numpy(), J_gate) and np.array_equal(K.cpu().numpy(), K_gate))
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = shard.max_over_ranks(ms, dev)
     ctx.sync_status()
@@ -696,8 +701,7 @@ def main():
     def step_e2e():
         Cd.copy_(Ch, non_blocking=True)
         Dd.copy_(Dh, non_blocking=True)
-        ctx.build_J(Dd, J, rho)
-        ctx.build_K(Cd, s, K)
+        ctx.build_JK(Dd, Cd, s, J, rho, K)
         ctx.energy(Dd, J, K, rho)
         Jh.copy_(J, non_blocking=True)
         Kh.copy_(K, non_blocking=True)
@@ -737,6 +741,8 @@ def main():
                    "slice_count": "fixed for every step (5 = Table 1 level 2's count, the first level meeting "
                                   "max|dK| <= 1e-10 max|K|)" if s == 5 else "fixed for every step", "l2": "inputs larger than L2 (B %.1f GB)" % (B_bytes / 1e9),
                    "cluster_pairs": args.cluster_pairs,
+                   "jk_overlap": "rho and J on %d CTAs per SM beside the X split (df_build_JK)" % args.jk_overlap
+                                 if args.jk_overlap else "J, then K, in one stream",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": FK / (ms_e2e * 1e-3) / 1e12 * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
@@ -746,7 +752,8 @@ def main():
                      "traffic": recorded_traffic(kname, w.name, s, args.cluster_pairs),
                      "peak_source": "bf16_tflops_sustained (%s)" % src,
                      "algorithmic": "s(s+1)/2 slice-pair products x 2 flops per multiply-add, no padding"},
-        "accuracy": {"max_dK_rel_vs_fp64": dK, "dE_vs_fp64": dE, "gate_1e-10": dK <= 1e-10},
+        "accuracy": {"max_dK_rel_vs_fp64": dK, "dE_vs_fp64": dE, "gate_1e-10": dK <= 1e-10,
+                     "jk_bit_identical_to_separate_builds": jk_same},
         "fp64_native": {"k_build_ms": ms_fp64, "tflops": FK / (ms_fp64 * 1e-3) / 1e12,
                         "speedup_of_int8": ms_fp64 / (phases_k_ms(phases, args.steps))},
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},

@@ -138,6 +138,24 @@ df_status df_build_J(df_ctx *ctx, const double *D_dev, double *J_dev, double *rh
 df_status df_build_K(df_ctx *ctx, const double *C_dev, int nocc, int nslices, double *K_dev,
                      df_kstats *stats, void *stream);
 
+/* The Coulomb and the exchange build of one density in a single call
+ * (Section 2.1, Eqs. df-j-1/2 and df-k-1/2): the results, bit for bit, of
+ * df_build_J(ctx, D_dev, J_dev, rho_dev, stream) followed by
+ * df_build_K(ctx, C_dev, nocc, nslices, K_dev, stats, stream), with the same
+ * arguments, ownership and errors.  For an emulated count (1..8, or -1 at a
+ * level that runs slices) the FP64 rho and J kernels run on an internal
+ * high-priority stream of the context, forked from `stream` after the first
+ * exchange GEMM and joined back before the second: they share the SMs with
+ * the X split (rho and J are bound by GB300's FP64 pipe, the X split by HBM
+ * and integer work), from short grids of a few CTAs per SM
+ * (DF_OPT_JK_OVERLAP).  Native FP64 (0), the learned counts (-2 at a level
+ * above 0), a block-sparse B (df_sparsity below 1, with DF_OPT_SPARSE on) and
+ * DF_OPT_JK_OVERLAP = 0 run the two builds in order in `stream`.  Calls on
+ * one context must not overlap (they share the internal stream and its work
+ * counters). */
+df_status df_build_JK(df_ctx *ctx, const double *D_dev, const double *C_dev, int nocc, int nslices,
+                      double *J_dev, double *rho_dev, double *K_dev, df_kstats *stats, void *stream);
+
 /* Exchange build with one slice count per auxiliary block (host array of
  * ceil(naux/128) entries, each 1..8), given by the caller; no check. */
 df_status df_build_K_blocks(df_ctx *ctx, const double *C_dev, int nocc, const int *slices_per_block,
@@ -414,6 +432,10 @@ df_status df_sparsity(const df_ctx *ctx, double *frac_ktiles, double *frac_chunk
 /* DF_OPT_SPARSE — whether the builds use the block sparsity of a screened B
  * (df_sparsity): 1 (default) when df_setup found zero chunks, 0 never. */
 #define DF_OPT_SPARSE 2
+/* DF_OPT_JK_OVERLAP — CTAs per SM of the rho and J kernels that df_build_JK
+ * runs beside the X split: 1..4 (default 4, the fastest at 240 atoms), 0 = no
+ * overlap (J, then K, in the caller's stream). */
+#define DF_OPT_JK_OVERLAP 3
 df_status df_set_option(df_ctx *ctx, int option, int value);
 
 #ifdef __cplusplus

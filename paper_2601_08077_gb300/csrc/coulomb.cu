@@ -38,63 +38,154 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One CTA per P.  Warp w takes rows mu = w, w + 8, ...; lanes stride nu >= mu.
-// With masks a lane skips the nu of zero chunks (no load: the bytes are not
-// fetched) and keeps the dense order of the rest, so rho is bit-identical to
-// the dense sum (a skipped term is an exact zero).
-template <bool kPacked>
-__global__ void __launch_bounds__(256) rho_kernel(const double *__restrict__ B, const double *__restrict__ D,
-                                                  int nao, double *__restrict__ rho,
-                                                  const uint32_t *__restrict__ mask_mu) {
-  const int P = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double *BP = B + (long long)P * (kPacked ? (long long)nao * (nao + 1) / 2 : (long long)nao * nao);
-  double off = 0.0, dia = 0.0;
-  for (int mu = warp; mu < nao; mu += 8) {
-    // brow[nu] is B_P mu nu for nu >= mu in either layout
-    const double *brow = kPacked ? BP + packed_row(mu, nao) - mu : BP + (long long)mu * nao;
-    const double *drow = D + (long long)mu * nao;
-    if (lane == 0) dia = fma(__ldg(brow + mu), __ldg(drow + mu), dia);
-    if (!mask_mu) {
-      for (int nu = mu + 1 + lane; nu < nao; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+// Work items of a launch: with a null counter the CTA takes its own index
+// once; otherwise the CTAs of a short grid (a few per SM, sharing the SMs
+// with another kernel) take items from the counter until they run out.  The
+// value is uniform over the CTA.
+__device__ __forceinline__ int take_item(int *work, int *slot) {
+  if (threadIdx.x == 0) *slot = atomicAdd(work, 1);
+  __syncthreads();
+  const int v = *slot;
+  __syncthreads();
+  return v;
+}
+
+// The strictly upper elements of B_P in row-pair order: pair q < nao/2 is
+// row q from nu = q + 1 followed by row nao-1-q from nu = nao-q (nao - 1
+// elements together, so every pair has the same length); for odd nao the
+// middle row, q = nao/2, comes last alone.  Thread t of the CTA takes the
+// elements t, t + 256, t + 512, ...: each warp reads 32 consecutive values of
+// one row, and no thread has a per-row tail.
+struct PairStream {
+  int q, e;       // the current element: offset e in pair q
+  int nao, L;     // L = nao - 1, the length of a full pair
+  __device__ __forceinline__ void init(int j0, int n) {
+    nao = n;
+    L = n - 1;
+    q = j0 / L;
+    e = j0 - q * L;
+  }
+  __device__ __forceinline__ bool valid() const {
+    return 2 * q + 1 < nao || (2 * q + 1 == nao && e < nao - 1 - q);
+  }
+  // (mu, nu), nu > mu, of the current element
+  __device__ __forceinline__ void at(int &mu, int &nu) const {
+    if (e < nao - 1 - q) {
+      mu = q;
+      nu = q + 1 + e;
     } else {
-      // the warp's 32-wide windows of the dense loop; a window whose one or two
-      // chunks are all zero is skipped as a whole (no loads)
-      const uint32_t mk = __ldg(mask_mu + mu);
-      for (int base = mu + 1; base < nao; base += 32) {
-        if (!(((mk >> (base >> 6)) | (mk >> ((base + 31) >> 6))) & 1u)) continue;
-        const int nu = base + lane;
-        if (nu < nao && ((mk >> (nu >> 6)) & 1u)) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+      mu = nao - 1 - q;
+      nu = e + 1;
+    }
+  }
+  __device__ __forceinline__ void advance(int step) {
+    e += step;
+    while (e >= L) {
+      e -= L;
+      ++q;
+    }
+  }
+};
+
+// rho_P for one P by one CTA of 256 threads:
+//   rho_P = sum_mu B_P mu mu D_mu mu + 2 sum_{mu < nu} B_P mu nu D_mu nu.
+// The diagonal terms are spread over the threads; the strictly upper ones
+// stream in row-pair order (PairStream), eight loads ahead of their FMAs (a
+// ring of registers, FMAs in stream order), so that a few CTAs per SM keep
+// enough bytes in flight to share the SM with another kernel.  With masks a
+// thread skips the elements of zero 64-wide chunks (no load, no FMA) and keeps
+// the order of the rest, so rho is bit-identical to the dense sum (a skipped
+// term is an exact zero).
+template <bool kPacked, bool kMasked>
+__device__ __forceinline__ void rho_one(const double *__restrict__ B, const double *__restrict__ D, int nao,
+                                        double *__restrict__ rho, const uint32_t *__restrict__ mask_mu, int P,
+                                        double *red) {
+  constexpr int kQ = 8;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double *BP = B + (long long)P * (kPacked ? (long long)nao * (nao + 1) / 2 : (long long)nao * nao);
+  auto badr = [&](int mu, int nu) -> const double * {
+    return kPacked ? BP + packed_row(mu, nao) + (nu - mu) : BP + (long long)mu * nao + nu;
+  };
+  double dia = 0.0;
+  for (int mu = tid; mu < nao; mu += 256) dia = fma(__ldg(badr(mu, mu)), __ldg(D + (long long)mu * nao + mu), dia);
+  double off = 0.0;
+  const long long total = (long long)nao * (nao - 1) / 2;
+  if (total > tid) {
+    PairStream ps;
+    ps.init(tid, nao);
+    double bq[kQ], dq[kQ];
+    bool lq[kQ];
+    auto fill = [&](int k) {
+      bq[k] = 0.0;
+      dq[k] = 0.0;
+      lq[k] = false;
+      if (ps.valid()) {
+        int mu, nu;
+        ps.at(mu, nu);
+        if (!kMasked || ((__ldg(mask_mu + mu) >> (nu >> 6)) & 1u)) {
+          bq[k] = __ldg(badr(mu, nu));
+          dq[k] = __ldg(D + (long long)mu * nao + nu);
+          lq[k] = true;
+        }
+      }
+      ps.advance(256);
+    };
+#pragma unroll
+    for (int k = 0; k < kQ; ++k) fill(k);
+    const long long mine = (total - tid + 255) / 256;
+    const int rounds = (int)((mine + kQ - 1) / kQ);
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+      for (int k = 0; k < kQ; ++k) {
+        if (!kMasked || lq[k]) off = fma(bq[k], dq[k], off);
+        fill(k);
       }
     }
   }
   double v = 2.0 * off + dia;
   v = warp_sum(v);
-  __shared__ double red[8];
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += red[w];
-    rho[P] = s;
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    rho[P] = t;
+  }
+  __syncthreads();
+}
+
+// One CTA per P (work == null), or a short grid taking P from the counter.
+// At most 48 registers (64 with masks), like the J kernel.
+template <bool kPacked, bool kMasked>
+__global__ void __launch_bounds__(256, kMasked ? 4 : 5) rho_kernel(const double *__restrict__ B, const double *__restrict__ D,
+                                                     int naux, int nao, double *__restrict__ rho,
+                                                     const uint32_t *__restrict__ mask_mu, int *__restrict__ work) {
+  __shared__ double red[8];
+  __shared__ int slot;
+  if (!work) {
+    rho_one<kPacked, kMasked>(B, D, nao, rho, mask_mu, blockIdx.x, red);
+    return;
+  }
+  for (;;) {
+    const int P = take_item(work, &slot);
+    if (P >= naux) break;
+    rho_one<kPacked, kMasked>(B, D, nao, rho, mask_mu, P, red);
   }
 }
 
 // J_mn = sum_P B_Pmn rho_P over the upper triangle, written to both halves.
-// CTA (x, y) takes elements x*256 .. of the row pair (y, nao-1-y): row y from
+// Item (x, y) takes elements x*256 .. of the row pair (y, nao-1-y): row y from
 // column y, then row nao-1-y from its diagonal (nao + 1 elements per pair, one
-// row alone in the middle when nao is odd), so every CTA has the same work.
-// Each element's sum runs over P in ascending order, one FMA per P.
+// row alone in the middle when nao is odd), so every item has the same work.
+// Each element's sum runs over P in ascending order, one FMA per P, with
+// eight loads of B ahead of their FMAs.
 template <bool kPacked>
-__global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__ B, const double *__restrict__ rho,
-                                                      int naux, int nao, double *__restrict__ J,
-                                                      const uint32_t *__restrict__ mask_mu) {
-  extern __shared__ double srho[];
-  for (int i = threadIdx.x; i < naux; i += blockDim.x) srho[i] = rho[i];
-  __syncthreads();
-  const int m0 = blockIdx.y, m1 = nao - 1 - m0;
+__device__ __forceinline__ void coulomb_one(const double *__restrict__ B, const double *srho, int naux, int nao,
+                                            double *__restrict__ J, const uint32_t *__restrict__ mask_mu, int x,
+                                            int y) {
+  const int m0 = y, m1 = nao - 1 - m0;
   const int len0 = nao - m0, len1 = m1 > m0 ? nao - m1 : 0;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = x * blockDim.x + threadIdx.x;
   if (e >= len0 + len1) return;
   const int mu = e < len0 ? m0 : m1;
   const int nu = e < len0 ? m0 + e : m1 + (e - len0);
@@ -107,21 +198,43 @@ __global__ void __launch_bounds__(256) coulomb_kernel(const double *__restrict__
     J[(long long)nu * nao + mu] = 0.0;
     return;
   }
+  const double *bp = B + off;
   double acc = 0.0;
   int P = 0;
-  for (; P + 4 <= naux; P += 4) {
-    const double b0 = __ldg(B + (P + 0) * stride + off);
-    const double b1 = __ldg(B + (P + 1) * stride + off);
-    const double b2 = __ldg(B + (P + 2) * stride + off);
-    const double b3 = __ldg(B + (P + 3) * stride + off);
-    acc = fma(b0, srho[P + 0], acc);
-    acc = fma(b1, srho[P + 1], acc);
-    acc = fma(b2, srho[P + 2], acc);
-    acc = fma(b3, srho[P + 3], acc);
+  for (; P + 8 <= naux; P += 8) {
+    double b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) b[q] = __ldg(bp + (P + q) * stride);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc = fma(b[q], srho[P + q], acc);
   }
-  for (; P < naux; ++P) acc = fma(__ldg(B + P * stride + off), srho[P], acc);
+  for (; P < naux; ++P) acc = fma(__ldg(bp + P * stride), srho[P], acc);
   J[jmn] = acc;
   J[(long long)nu * nao + mu] = acc;
+}
+
+// Grid (gx, gy) of items (work == null), or a short grid taking item
+// x + gx y from the counter.  At most 48 registers, so that a short grid of a
+// few CTAs per SM leaves room for the X split's CTAs.
+template <bool kPacked>
+__global__ void __launch_bounds__(256, 5) coulomb_kernel(const double *__restrict__ B,
+                                                         const double *__restrict__ rho, int naux, int nao,
+                                                         double *__restrict__ J,
+                                                         const uint32_t *__restrict__ mask_mu,
+                                                         int *__restrict__ work, int gx, int nitems) {
+  extern __shared__ double srho[];
+  __shared__ int slot;
+  for (int i = threadIdx.x; i < naux; i += blockDim.x) srho[i] = rho[i];
+  __syncthreads();
+  if (!work) {
+    coulomb_one<kPacked>(B, srho, naux, nao, J, mask_mu, blockIdx.x, blockIdx.y);
+    return;
+  }
+  for (;;) {
+    const int it = take_item(work, &slot);
+    if (it >= nitems) break;
+    coulomb_one<kPacked>(B, srho, naux, nao, J, mask_mu, it % gx, it / gx);
+  }
 }
 
 // Partial sums: [0] sum D.J, [1] sum rho.rho, [2] sum D.K, one triple per block.
@@ -366,16 +479,24 @@ cudaError_t launch_density_change(const double *D, double *Dprev, bool have_prev
 }
 
 cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st,
-                       const uint32_t *mask_mu, bool packed) {
-  if (packed)
-    rho_kernel<true><<<naux, 256, 0, st>>>(B, D, nao, rho, mask_mu);
-  else
-    rho_kernel<false><<<naux, 256, 0, st>>>(B, D, nao, rho, mask_mu);
+                       const uint32_t *mask_mu, bool packed, int *work, int grid) {
+  const unsigned g = work ? (unsigned)grid : (unsigned)naux;
+  if (packed) {
+    if (mask_mu)
+      rho_kernel<true, true><<<g, 256, 0, st>>>(B, D, naux, nao, rho, mask_mu, work);
+    else
+      rho_kernel<true, false><<<g, 256, 0, st>>>(B, D, naux, nao, rho, mask_mu, work);
+  } else {
+    if (mask_mu)
+      rho_kernel<false, true><<<g, 256, 0, st>>>(B, D, naux, nao, rho, mask_mu, work);
+    else
+      rho_kernel<false, false><<<g, 256, 0, st>>>(B, D, naux, nao, rho, mask_mu, work);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st,
-                           const uint32_t *mask_mu, bool packed) {
+                           const uint32_t *mask_mu, bool packed, int *work, int grid) {
   const size_t sm = (size_t)naux * sizeof(double);
   static size_t attr = 48 * 1024;
   if (sm > attr) {
@@ -385,11 +506,12 @@ cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao
     if (e != cudaSuccess) return e;
     attr = sm;
   }
-  dim3 grid((nao + 1 + 255) / 256, (nao + 1) / 2);
+  const int gx = (nao + 1 + 255) / 256, gy = (nao + 1) / 2;
+  const dim3 g = work ? dim3((unsigned)grid) : dim3(gx, gy);
   if (packed)
-    coulomb_kernel<true><<<grid, 256, sm, st>>>(B, rho, naux, nao, J, mask_mu);
+    coulomb_kernel<true><<<g, 256, sm, st>>>(B, rho, naux, nao, J, mask_mu, work, gx, gx * gy);
   else
-    coulomb_kernel<false><<<grid, 256, sm, st>>>(B, rho, naux, nao, J, mask_mu);
+    coulomb_kernel<false><<<g, 256, sm, st>>>(B, rho, naux, nao, J, mask_mu, work, gx, gx * gy);
   return cudaGetLastError();
 }
 

@@ -257,7 +257,8 @@ long long xdigit_ld(int nocc) { return round_up((long long)kBlock * nocc, 64); }
 
 namespace df {
 
-df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_planes, cudaStream_t st) {
+df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_planes, cudaStream_t st,
+                  cudaEvent_t after_gemm1) {
   int smax = 0;
   for (int b = 0; b < c->nblk; ++b) {
     if (sb[b] < 1 || sb[b] > c->s_max) return record(c, DF_ERR_ARG);
@@ -283,6 +284,7 @@ df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_pla
     PhaseTimer t(c, DF_PHASE_GEMM1, st);
     DF_TRY(c, df::launch_slice_gemm(p, ta, tb, st));
   }
+  if (after_gemm1) DF_TRY(c, cudaEventRecord(after_gemm1, st));
   // 3. X -> per-(block, mu) digit planes
   const long long kb_ld = df::xdigit_ld(nocc);
   {
@@ -427,9 +429,11 @@ df_status df_create(df_ctx **out, int nao, int naux, int nocc_max, int s_max) {
       }
     }
     c->nsplit = best;
+    c->nsm = nsm;
   }
   if (e == cudaSuccess) e = alloc(c, &c->Rp, (size_t)c->nblk * c->nsplit * nao * nao);
   if (e == cudaSuccess) e = alloc(c, &c->rho, (size_t)naux);
+  if (e == cudaSuccess) e = alloc(c, &c->jk_work, (size_t)2);
   if (e == cudaSuccess) e = alloc(c, &c->epart, (size_t)3 * 296);
   if (e == cudaSuccess) e = alloc(c, &c->E, (size_t)4);
   if (e == cudaSuccess) e = alloc(c, &c->sblk, (size_t)c->nblk);
@@ -467,6 +471,10 @@ void df_destroy(df_ctx *c) {
   cudaFree(c->rowE);
   cudaFree(c->Rp);
   cudaFree(c->rho);
+  cudaFree(c->jk_work);
+  if (c->jk_stream) cudaStreamDestroy(c->jk_stream);
+  if (c->jk_fork) cudaEventDestroy(c->jk_fork);
+  if (c->jk_join) cudaEventDestroy(c->jk_join);
   cudaFree(c->epart);
   cudaFree(c->E);
   cudaFree(c->sblk);
@@ -521,6 +529,10 @@ df_status df_set_option(df_ctx *c, int option, int value) {
     case DF_OPT_SPARSE:
       if (value < 0 || value > 1) return DF_ERR_ARG;
       c->sparse_opt = value;
+      return DF_OK;
+    case DF_OPT_JK_OVERLAP:
+      if (value < 0 || value > 4) return DF_ERR_ARG;
+      c->jk_ctas = value;
       return DF_OK;
   }
   return DF_ERR_ARG;
@@ -653,6 +665,76 @@ df_status df_build_J(df_ctx *c, const double *D, double *J, double *rho, void *s
   // the density change since the last Coulomb build (an input of the learned slice counts)
   DF_TRY(c, df::launch_density_change(D, c->Dprev, c->have_Dprev, (long long)c->nao * c->nao, c->dD_part, c->dD, st));
   c->have_Dprev = true;
+  return DF_OK;
+}
+
+namespace {
+
+// The internal stream and events of df_build_JK (created on first use).
+df_status jk_streams(df_ctx *c) {
+  if (c->jk_stream) return DF_OK;
+  int lo = 0, hi = 0;
+  DF_TRY(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  DF_TRY(c, cudaStreamCreateWithPriority(&c->jk_stream, cudaStreamNonBlocking, hi));
+  DF_TRY(c, cudaEventCreateWithFlags(&c->jk_fork, cudaEventDisableTiming));
+  DF_TRY(c, cudaEventCreateWithFlags(&c->jk_join, cudaEventDisableTiming));
+  return DF_OK;
+}
+
+}  // namespace
+
+df_status df_build_JK(df_ctx *c, const double *D, const double *C, int nocc, int nslices, double *J, double *rho,
+                      double *K, df_kstats *stats, void *stream) {
+  if (!c || !D || !J || !C || !K || nocc <= 0 || nocc > c->nocc_max || nslices < -2 || nslices > c->s_max)
+    return record(c, DF_ERR_ARG);
+  if (!c->ready) return record(c, DF_ERR_STATE);
+  int level = -1, s = nslices;
+  if (s < 0) {
+    level = c->level;
+    s = df::level_count(c, level);
+  }
+  if (s > c->s_max) return record(c, DF_ERR_ARG);
+  // the native FP64 build, the learned counts, a block-sparse B (whose
+  // masked kernels take more registers than an SM shared with the X split
+  // leaves) and the no-overlap option run the two builds one after the other
+  if (c->jk_ctas == 0 || s == 0 || (nslices == -2 && c->level > 0) || df::use_mask_mu(c)) {
+    df_status r = df_build_J(c, D, J, rho, stream);
+    return r == DF_OK ? df_build_K(c, C, nocc, nslices, K, stats, stream) : r;
+  }
+  df_status r = jk_streams(c);
+  if (r != DF_OK) return r;
+  cudaStream_t st = as_stream(stream), side = c->jk_stream;
+  int sb[4096];
+  if (c->nblk > 4096) return record(c, DF_ERR_ARG);
+  for (int b = 0; b < c->nblk; ++b) sb[b] = s;
+  // the exchange front (C split, first GEMM, X split) in the caller's stream;
+  // the Coulomb build forks after the first GEMM, whose persistent grid fills
+  // every SM, and runs beside the X split: rho and J are bound by the FP64
+  // pipe, the X split by HBM and integer work, so they share the SMs
+  r = df::k_front(c, C, nocc, sb, 0, st, c->jk_fork);
+  if (r != DF_OK) return r;
+  DF_TRY(c, cudaStreamWaitEvent(side, c->jk_fork, 0));
+  double *rr = rho ? rho : c->rho;
+  const int grid = c->jk_ctas * (c->nsm > 0 ? c->nsm : 1);
+  DF_TRY(c, cudaMemsetAsync(c->jk_work, 0, 2 * sizeof(int), side));
+  {
+    PhaseTimer t(c, DF_PHASE_RHO, side);
+    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, rr, side, nullptr, c->packed, c->jk_work, grid));
+  }
+  {
+    PhaseTimer t(c, DF_PHASE_COULOMB, side);
+    DF_TRY(c, df::launch_coulomb(c->B, rr, c->naux, c->nao, J, side, nullptr, c->packed, c->jk_work + 1, grid));
+  }
+  if (rho && rho != c->rho)
+    DF_TRY(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * c->naux, cudaMemcpyDeviceToDevice, side));
+  DF_TRY(c, cudaEventRecord(c->jk_join, side));
+  // the second GEMM's persistent grid waits for whole SMs: join first
+  DF_TRY(c, cudaStreamWaitEvent(st, c->jk_join, 0));
+  r = df::k_back(c, nocc, K, st);
+  if (r != DF_OK) return r;
+  DF_TRY(c, df::launch_density_change(D, c->Dprev, c->have_Dprev, (long long)c->nao * c->nao, c->dD_part, c->dD, st));
+  c->have_Dprev = true;
+  fill_stats(stats, c, sb, level);
   return DF_OK;
 }
 

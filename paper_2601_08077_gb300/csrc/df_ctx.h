@@ -23,6 +23,14 @@ struct df_ctx {
   long long *Rp = nullptr;  // int64 partials of the second GEMM [nblk][nsplit][nao][nao]
   int nsplit = 1;
   double *rho = nullptr;
+  // df_build_JK: rho and J on a high-priority internal stream beside the X
+  // split, from short grids of jk_ctas CTAs per SM taking items from the two
+  // counters jk_work (0: everything in the caller's stream, in order)
+  int *jk_work = nullptr;
+  int jk_ctas = 4;
+  int nsm = 0;
+  cudaStream_t jk_stream = nullptr;
+  cudaEvent_t jk_fork = nullptr, jk_join = nullptr;
   double *epart = nullptr;
   double *E = nullptr;
   int *sblk = nullptr;      // device per-block slice counts
@@ -88,7 +96,9 @@ inline const uint32_t *use_mask_tile(const df_ctx *c) { return c->sparse && c->s
 // the front uploads sb, splits C into c_planes digit planes (>= max sb), runs
 // the first GEMM and the X split; the back runs the second GEMM and the
 // reduce into K.  Both asynchronous on st.
-df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_planes, cudaStream_t st);
+// after_gemm1 (optional): an event recorded in st right after the first GEMM.
+df_status k_front(df_ctx *c, const double *C, int nocc, const int *sb, int c_planes, cudaStream_t st,
+                  cudaEvent_t after_gemm1 = nullptr);
 df_status k_back(df_ctx *c, int nocc, double *K, cudaStream_t st);
 // The slice count run at a Table 1 level under the context's controller
 // settings (0 = native FP64).

@@ -168,10 +168,14 @@ int fixed_point_shift(int s, long long k);
 // mask_mu (optional, block-sparse B): per mu, bit c set when some B_P mu nu
 // with nu in [64c, 64c + 64) is nonzero; null = dense.
 // packed: B holds per P the upper triangle row by row ([naux][nao (nao + 1) / 2]).
+// work (optional): a zeroed item counter; then `grid` CTAs take the items from
+// it (a short grid sharing the SMs with a concurrent kernel), else one CTA
+// per item.  Either way every rho_P and J_mn is summed in the same order.
 cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st,
-                       const uint32_t *mask_mu = nullptr, bool packed = false);
+                       const uint32_t *mask_mu = nullptr, bool packed = false, int *work = nullptr, int grid = 0);
 cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st,
-                           const uint32_t *mask_mu = nullptr, bool packed = false);
+                           const uint32_t *mask_mu = nullptr, bool packed = false, int *work = nullptr,
+                           int grid = 0);
 // The masks of a packed B (pair flags through stream-ordered scratch of nao (nao + 1) / 2 bytes).
 cudaError_t launch_pair_masks_packed(const double *Bp, int naux, int nao, uint32_t *mask_mu, uint32_t *mask_tile,
                                      cudaStream_t st);

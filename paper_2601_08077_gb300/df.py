@@ -19,6 +19,7 @@ S_MAX = 8
 AUX_BLOCK = 128
 OPT_CLUSTER_PAIRS = 1  # DF_OPT_CLUSTER_PAIRS
 OPT_SPARSE = 2         # DF_OPT_SPARSE
+OPT_JK_OVERLAP = 3     # DF_OPT_JK_OVERLAP
 PHASES = ("split_C", "gemm1", "split_X", "gemm2", "reduce", "rho", "coulomb", "energy")
 
 _STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA or cuBLAS call failed", -3: "device allocation failed",
@@ -69,6 +70,7 @@ def lib():
         L.df_setup_packed.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), V]
         L.df_build_J.argtypes = [P, P, P, P, V]
         L.df_build_K.argtypes = [P, P, I, I, P, ctypes.POINTER(KStats), V]
+        L.df_build_JK.argtypes = [P, P, P, I, I, P, P, P, ctypes.POINTER(KStats), V]
         L.df_build_K_blocks.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(KStats), V]
         L.df_energy.argtypes = [P, P, P, P, P, ctypes.POINTER(ctypes.c_double), V]
         L.df_split_int8.argtypes = [P, I, I, I, I, P, P, V]
@@ -321,6 +323,20 @@ class Context:
                "df_build_K")
         return K, st
 
+    def build_JK(self, D, C, nslices: int, J=None, rho=None, K=None, stream=None):
+        """build_J(D) then build_K(C, nslices) in one call (rho and J beside the X split); (J, rho, K, stats)."""
+        nocc = C.shape[1]
+        if J is None:
+            J = torch.empty((self.nao, self.nao), dtype=torch.float64, device=D.device)
+        if rho is None:
+            rho = torch.empty(self.naux, dtype=torch.float64, device=D.device)
+        if K is None:
+            K = torch.empty((self.nao, self.nao), dtype=torch.float64, device=C.device)
+        st = KStats()
+        _check(lib().df_build_JK(self._h, _f64(D), _f64(C), nocc, int(nslices), _f64(J), _f64(rho), _f64(K),
+                                 ctypes.byref(st), _stream(stream)), "df_build_JK")
+        return J, rho, K, st
+
     def build_K_blocks(self, C, slices, K=None, stream=None):
         nocc = C.shape[1]
         if K is None:
@@ -359,6 +375,10 @@ class Context:
     def set_sparse(self, on: bool):
         """DF_OPT_SPARSE: use the block sparsity of a screened B (default) or run dense."""
         _check(lib().df_set_option(self._h, OPT_SPARSE, 1 if on else 0), "df_set_option")
+
+    def set_jk_overlap(self, ctas_per_sm: int):
+        """DF_OPT_JK_OVERLAP: CTAs per SM of rho and J beside the X split in build_JK (0 = in order)."""
+        _check(lib().df_set_option(self._h, OPT_JK_OVERLAP, int(ctas_per_sm)), "df_set_option")
 
     def phase_times(self):
         """{phase: (total ms, records)} since the last read (waits for the events)."""
