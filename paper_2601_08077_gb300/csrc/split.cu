@@ -16,6 +16,7 @@
 #include "df_internal.h"
 
 #include <climits>
+#include <type_traits>
 
 namespace df {
 
@@ -235,6 +236,9 @@ __global__ void split_cols_bf16_kernel(const double *__restrict__ C, int nrows, 
 // keys and a second re-reads the row (256 KB at most, mostly from DRAM) for
 // the digits.  Two consecutive orbitals per thread (16-byte loads, 4-byte
 // stores) when nocc is even.
+template <int M>
+using Mode = std::integral_constant<int, M>;  // digits_pass: 0 digits, 1 and keys, 2 and threshold bits
+
 constexpr int kSplitXThreads = 256;
 constexpr int kSplitXMinBlocks = 6;  // 40 registers: six rows in flight per SM (four at 51 measured slower)
 constexpr int kP1 = 4;  // loads in flight per thread in the first pass (8 measured slower)
@@ -305,9 +309,28 @@ __global__ void __launch_bounds__(kSplitXThreads, kSplitXMinBlocks) split_xblock
     }
   };
 
+  // With the first GEMM's bound g (the largest bitlen(|R|) + k of the row):
+  // whether some element reaches 127/128 2^g once rounded to FP64 (only an
+  // element with bitlen(|R|) + k == g can: its normalised mantissa M must
+  // round to at least 127 2^46 on 53 bits, i.e. M >= 127 2^57 - 2^10, the tie
+  // going to the even 127 2^46), and whether the bound holds (no element above
+  // g, some element at g).  Bits: 1 reaches, 2 above g, 4 at g.
+  constexpr uint64_t kTopM = 0xFDFFFFFFFFFFFC00ull;
+  int tbits = 0;
+  auto thr = [&](long long r, int k, int g) {
+    if (r == 0) return;
+    const uint64_t u = r < 0 ? (uint64_t)(-(r + 1)) + 1ull : (uint64_t)r;
+    const int lz = __clzll((long long)u);
+    const int E = 64 - lz + k;
+    tbits |= (E > g ? 2 : 0) | (E == g ? (4 | ((u << lz) >= kTopM ? 1 : 0)) : 0);
+  };
+
   // The digits of the whole row (zero digits in the padding) with exponent e;
-  // with keys, the magnitude keys of the row's elements are taken on the way.
-  auto digits_pass = [&](int e, bool keys) {
+  // mode 1 takes the magnitude keys of the row's elements on the way, mode 2
+  // the threshold bits against the bound g (= e).
+  auto digits_pass = [&](int e, auto mode_c) {
+    constexpr int mode = decltype(mode_c)::value;
+    constexpr bool keys = mode == 1, tb = mode == 2;
     if ((nocc & 1) == 0) {
       const int hp = nocc >> 1;
       constexpr long long kBias = 0x0080808080808080ll;  // 128 in each of the seven low bytes
@@ -341,6 +364,10 @@ __global__ void __launch_bounds__(kSplitXThreads, kSplitXMinBlocks) split_xblock
               take(v[r].x, kp + eI[i]);
               take(v[r].y, kp + eI[i + 1]);
             }
+            if (tb) {
+              thr(v[r].x, kp + eI[i], e);
+              thr(v[r].y, kp + eI[i + 1], e);
+            }
             M0 += scaled_rne_i64(v[r].x, kp + eI[i], e);
             M1 += scaled_rne_i64(v[r].y, kp + eI[i + 1], e);
           }
@@ -359,6 +386,7 @@ __global__ void __launch_bounds__(kSplitXThreads, kSplitXMinBlocks) split_xblock
           const int i = k - pl * nocc;
           const long long r = row0[pl * pstride + i];
           if (keys) take(r, eP[pl] + eI[i]);
+          if (tb) thr(r, eP[pl] + eI[i], e);
           balanced_digits(scaled_rne_i64(r, eP[pl] + eI[i], e), d);
         } else {
 #pragma unroll
@@ -401,16 +429,38 @@ __global__ void __launch_bounds__(kSplitXThreads, kSplitXMinBlocks) split_xblock
     __syncthreads();
   };
 
-  if (rowE) {
-    // One read of R: the row's largest |X| lies in [2^(E-1), 2^E] for the first
-    // GEMM's bound E, so its exponent is E, or E + 1 when it reaches 127/128 2^E
-    // (or an all-zero row after rounding): digits with the guess, keys on the
-    // way, and a second pass only for a row whose exponent differs.
-    const int g = __ldg(rowE + b * nao + mu);
+  const int g = rowE ? __ldg(rowE + b * nao + mu) : kRowBoundNone;
+  if (rowE && g != kRowBoundNone && g > -1000 && g < 1000) {
+    // One read of R: the row's largest |X| lies in [2^(g-1), 2^g] for the first
+    // GEMM's bound g, so its exponent is g, or g + 1 when some element reaches
+    // 127/128 2^g: digits with g and the threshold bits on the way, a second
+    // pass only for a row that reaches it (far from the FP64 range's ends, so
+    // that no element near 2^g is flushed).  Should the bound not hold, the
+    // exact keys decide, as below.
+    digits_pass(g, Mode<2>{});
+    __shared__ int tsh;
+    if (threadIdx.x == 0) tsh = 0;
+    __syncthreads();
+    const int wb = __reduce_or_sync(0xffffffffu, tbits);
+    if ((threadIdx.x & 31) == 0 && wb) atomicOr(&tsh, wb);
+    __syncthreads();
+    const int bits = tsh;
+    if ((bits & 6) == 4) {
+      const int e = (bits & 1) ? g + 1 : g;
+      if (threadIdx.x == 0) eX[b * nao + mu] = e;
+      if (e != g) digits_pass(e, Mode<0>{});
+    } else {
+      digits_pass(g, Mode<1>{});
+      reduce_keys();
+      if (e_sh != g) digits_pass(e_sh, Mode<0>{});
+    }
+  } else if (rowE) {
+    // an all-zero row (or a bound near the FP64 range's ends): the exact keys
+    // on the way, a second pass if the exponent differs from the guess
     const int e0 = g == kRowBoundNone ? exponent_from_max_bits_dev(0ull) : g;
-    digits_pass(e0, true);
+    digits_pass(e0, Mode<1>{});
     reduce_keys();
-    if (e_sh != e0) digits_pass(e_sh, false);
+    if (e_sh != e0) digits_pass(e_sh, Mode<0>{});
   } else {
     // two passes: the keys (four loads in flight per thread), then the digits
     if ((nocc & 1) == 0) {
@@ -448,7 +498,7 @@ __global__ void __launch_bounds__(kSplitXThreads, kSplitXMinBlocks) split_xblock
       }
     }
     reduce_keys();
-    digits_pass(e_sh, false);
+    digits_pass(e_sh, Mode<0>{});
   }
 }
 
