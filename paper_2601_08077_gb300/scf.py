@@ -66,9 +66,8 @@ def run(ctx, h, S, nocc: int, E_nuc: float, mode: str = "rule", level0_slices: i
         D = 2.0 * C_occ @ C_occ.T
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        ctx.build_J(D, J, rho)
         ns = {"fp64": 0, "fixed": fixed_slices}.get(mode, s)
-        ctx.build_K(C_occ, ns, K)
+        ctx.build_JK(D, C_occ, ns, J, rho, K)
         EJ, _, EK = ctx.energy(D, J, K, rho)
         e1.record()
         torch.cuda.synchronize()

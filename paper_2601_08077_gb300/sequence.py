@@ -4,8 +4,8 @@ Section 3.2's scheme on a synthetic sequence: iteration k uses orbitals C_k
 whose density differs from the converged D* by 0.1 10^-k (Frobenius).  The
 library's controller (df_adaptive_next: Table 1, monotone, iterations 0 and 1
 at level 4) picks each iteration's level from the relative change of the
-energy E_J + E_K; the build runs at that level's count (mode "rule",
-df_build_K with ADAPTIVE), with per-block counts from the attached network
+energy E_J + E_K; J and K of an iteration come from one df_build_JK call
+(rho and J beside the X split), at that level's count (mode "rule", ADAPTIVE), with per-block counts from the attached network
 (mode "learned", LEARNED: prediction, fallback, check and recompute all in
 the library), or in native FP64 (mode "fp64").  Optionally every iteration's
 K and energy are compared with the native-FP64 build of the same density
@@ -48,8 +48,7 @@ def run(ctx, orbitals, mode="rule", fp64_from_level=-1, level0_slices=0, compare
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        ctx.build_J(Dg, J, rho)
-        _, st = ctx.build_K(Cg, nslices, K)
+        _, _, _, st = ctx.build_JK(Dg, Cg, nslices, J, rho, K)
         E = ctx.energy(Dg, J, K, rho)
         e1.record()
         torch.cuda.synchronize()
