@@ -305,7 +305,7 @@ df_status df_batch_build_J(df_batch *b, const double *const *D, double *const *J
       df_ctx *c = b->ctx[i];
       cudaStream_t si = b->side[i % df_batch::kFan];
       const uint32_t *mk = df::use_mask_mu(c);
-      if (df::launch_rho(c->B, D[i], c->naux, c->nao, c->rho, si, mk, c->packed) != cudaSuccess) return DF_ERR_CUDA;
+      if (df::launch_rho(c->B, D[i], c->naux, c->nao, c->rho, si, mk, c->packed, nullptr, 0, c->sparse) != cudaSuccess) return DF_ERR_CUDA;
       if (df::launch_coulomb(c->B, c->rho, c->naux, c->nao, J[i], si, mk, c->packed) != cudaSuccess)
         return DF_ERR_CUDA;
     }

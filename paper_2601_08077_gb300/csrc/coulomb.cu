@@ -92,14 +92,10 @@ struct PairStream {
 // The diagonal terms are spread over the threads; the strictly upper ones
 // stream in row-pair order (PairStream), eight loads ahead of their FMAs (a
 // ring of registers, FMAs in stream order), so that a few CTAs per SM keep
-// enough bytes in flight to share the SM with another kernel.  With masks a
-// thread skips the elements of zero 64-wide chunks (no load, no FMA) and keeps
-// the order of the rest, so rho is bit-identical to the dense sum (a skipped
-// term is an exact zero).
-template <bool kPacked, bool kMasked>
+// enough bytes in flight to share the SM with another kernel.
+template <bool kPacked>
 __device__ __forceinline__ void rho_one(const double *__restrict__ B, const double *__restrict__ D, int nao,
-                                        double *__restrict__ rho, const uint32_t *__restrict__ mask_mu, int P,
-                                        double *red) {
+                                        double *__restrict__ rho, int P, double *red) {
   constexpr int kQ = 8;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double *BP = B + (long long)P * (kPacked ? (long long)nao * (nao + 1) / 2 : (long long)nao * nao);
@@ -114,19 +110,14 @@ __device__ __forceinline__ void rho_one(const double *__restrict__ B, const doub
     PairStream ps;
     ps.init(tid, nao);
     double bq[kQ], dq[kQ];
-    bool lq[kQ];
     auto fill = [&](int k) {
       bq[k] = 0.0;
       dq[k] = 0.0;
-      lq[k] = false;
       if (ps.valid()) {
         int mu, nu;
         ps.at(mu, nu);
-        if (!kMasked || ((__ldg(mask_mu + mu) >> (nu >> 6)) & 1u)) {
-          bq[k] = __ldg(badr(mu, nu));
-          dq[k] = __ldg(D + (long long)mu * nao + nu);
-          lq[k] = true;
-        }
+        bq[k] = __ldg(badr(mu, nu));
+        dq[k] = __ldg(D + (long long)mu * nao + nu);
       }
       ps.advance(256);
     };
@@ -137,7 +128,7 @@ __device__ __forceinline__ void rho_one(const double *__restrict__ B, const doub
     for (int r = 0; r < rounds; ++r) {
 #pragma unroll
       for (int k = 0; k < kQ; ++k) {
-        if (!kMasked || lq[k]) off = fma(bq[k], dq[k], off);
+        off = fma(bq[k], dq[k], off);
         fill(k);
       }
     }
@@ -154,22 +145,71 @@ __device__ __forceinline__ void rho_one(const double *__restrict__ B, const doub
   __syncthreads();
 }
 
+// rho_P for a B with zero 64-wide chunks (a Schwarz-screened B), row by row:
+// warp w takes rows mu = w, w + 8, ...; lanes stride nu > mu.  With masks a
+// warp skips each 32-wide window whose chunks are all zero as a whole (no
+// loads, no FMAs) and keeps the order of the rest; without (DF_OPT_SPARSE
+// off) it runs every window in the same order, so the two are bit-identical
+// (a skipped term is an exact zero).  The row-pair stream would visit every
+// element of the triangle to skip the zero ones.
+template <bool kPacked>
+__device__ __forceinline__ void rho_one_rows(const double *__restrict__ B, const double *__restrict__ D, int nao,
+                                             double *__restrict__ rho, const uint32_t *__restrict__ mask_mu, int P,
+                                             double *red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double *BP = B + (long long)P * (kPacked ? (long long)nao * (nao + 1) / 2 : (long long)nao * nao);
+  double off = 0.0, dia = 0.0;
+  for (int mu = warp; mu < nao; mu += 8) {
+    // brow[nu] is B_P mu nu for nu >= mu in either layout
+    const double *brow = kPacked ? BP + packed_row(mu, nao) - mu : BP + (long long)mu * nao;
+    const double *drow = D + (long long)mu * nao;
+    if (lane == 0) dia = fma(__ldg(brow + mu), __ldg(drow + mu), dia);
+    if (!mask_mu) {
+      for (int nu = mu + 1 + lane; nu < nao; nu += 32) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+    } else {
+      const uint32_t mk = __ldg(mask_mu + mu);
+      for (int base = mu + 1; base < nao; base += 32) {
+        if (!(((mk >> (base >> 6)) | (mk >> ((base + 31) >> 6))) & 1u)) continue;
+        const int nu = base + lane;
+        if (nu < nao && ((mk >> (nu >> 6)) & 1u)) off = fma(__ldg(brow + nu), __ldg(drow + nu), off);
+      }
+    }
+  }
+  double v = 2.0 * off + dia;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    rho[P] = t;
+  }
+  __syncthreads();
+}
+
 // One CTA per P (work == null), or a short grid taking P from the counter.
-// At most 48 registers (64 with masks), like the J kernel.
-template <bool kPacked, bool kMasked>
-__global__ void __launch_bounds__(256, kMasked ? 4 : 5) rho_kernel(const double *__restrict__ B, const double *__restrict__ D,
+// kRows: the row-by-row order of a B with zero chunks (masks optional).  At
+// most 48 registers, like the J kernel.
+template <bool kPacked, bool kRows>
+__global__ void __launch_bounds__(256, 5) rho_kernel(const double *__restrict__ B, const double *__restrict__ D,
                                                      int naux, int nao, double *__restrict__ rho,
                                                      const uint32_t *__restrict__ mask_mu, int *__restrict__ work) {
   __shared__ double red[8];
   __shared__ int slot;
   if (!work) {
-    rho_one<kPacked, kMasked>(B, D, nao, rho, mask_mu, blockIdx.x, red);
+    if (kRows)
+      rho_one_rows<kPacked>(B, D, nao, rho, mask_mu, blockIdx.x, red);
+    else
+      rho_one<kPacked>(B, D, nao, rho, blockIdx.x, red);
     return;
   }
   for (;;) {
     const int P = take_item(work, &slot);
     if (P >= naux) break;
-    rho_one<kPacked, kMasked>(B, D, nao, rho, mask_mu, P, red);
+    if (kRows)
+      rho_one_rows<kPacked>(B, D, nao, rho, mask_mu, P, red);
+    else
+      rho_one<kPacked>(B, D, nao, rho, P, red);
   }
 }
 
@@ -479,18 +519,19 @@ cudaError_t launch_density_change(const double *D, double *Dprev, bool have_prev
 }
 
 cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st,
-                       const uint32_t *mask_mu, bool packed, int *work, int grid) {
+                       const uint32_t *mask_mu, bool packed, int *work, int grid, bool rows) {
   const unsigned g = work ? (unsigned)grid : (unsigned)naux;
+  rows = rows || mask_mu;
   if (packed) {
-    if (mask_mu)
+    if (rows)
       rho_kernel<true, true><<<g, 256, 0, st>>>(B, D, naux, nao, rho, mask_mu, work);
     else
-      rho_kernel<true, false><<<g, 256, 0, st>>>(B, D, naux, nao, rho, mask_mu, work);
+      rho_kernel<true, false><<<g, 256, 0, st>>>(B, D, naux, nao, rho, nullptr, work);
   } else {
-    if (mask_mu)
+    if (rows)
       rho_kernel<false, true><<<g, 256, 0, st>>>(B, D, naux, nao, rho, mask_mu, work);
     else
-      rho_kernel<false, false><<<g, 256, 0, st>>>(B, D, naux, nao, rho, mask_mu, work);
+      rho_kernel<false, false><<<g, 256, 0, st>>>(B, D, naux, nao, rho, nullptr, work);
   }
   return cudaGetLastError();
 }

@@ -654,7 +654,7 @@ df_status df_build_J(df_ctx *c, const double *D, double *J, double *rho, void *s
   double *r = rho ? rho : c->rho;
   {
     PhaseTimer t(c, DF_PHASE_RHO, st);
-    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, r, st, df::use_mask_mu(c), c->packed));
+    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, r, st, df::use_mask_mu(c), c->packed, nullptr, 0, c->sparse));
   }
   {
     PhaseTimer t(c, DF_PHASE_COULOMB, st);
@@ -719,7 +719,7 @@ df_status df_build_JK(df_ctx *c, const double *D, const double *C, int nocc, int
   DF_TRY(c, cudaMemsetAsync(c->jk_work, 0, 2 * sizeof(int), side));
   {
     PhaseTimer t(c, DF_PHASE_RHO, side);
-    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, rr, side, nullptr, c->packed, c->jk_work, grid));
+    DF_TRY(c, df::launch_rho(c->B, D, c->naux, c->nao, rr, side, nullptr, c->packed, c->jk_work, grid, c->sparse));
   }
   {
     PhaseTimer t(c, DF_PHASE_COULOMB, side);

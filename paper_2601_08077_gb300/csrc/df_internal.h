@@ -171,8 +171,12 @@ int fixed_point_shift(int s, long long k);
 // work (optional): a zeroed item counter; then `grid` CTAs take the items from
 // it (a short grid sharing the SMs with a concurrent kernel), else one CTA
 // per item.  Either way every rho_P and J_mn is summed in the same order.
+// rows: rho in the row-by-row order of a B with zero chunks (taken whenever
+// mask_mu is given), else in row-pair order; the order is the B's, so a
+// screened B gives the same bits with and without its masks.
 cudaError_t launch_rho(const double *B, const double *D, int naux, int nao, double *rho, cudaStream_t st,
-                       const uint32_t *mask_mu = nullptr, bool packed = false, int *work = nullptr, int grid = 0);
+                       const uint32_t *mask_mu = nullptr, bool packed = false, int *work = nullptr, int grid = 0,
+                       bool rows = false);
 cudaError_t launch_coulomb(const double *B, const double *rho, int naux, int nao, double *J, cudaStream_t st,
                            const uint32_t *mask_mu = nullptr, bool packed = false, int *work = nullptr,
                            int grid = 0);
