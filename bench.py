@@ -757,7 +757,9 @@ def main():
                    "slice_count": "fixed for every step (5 = Table 1 level 2's count, the first level meeting "
                                   "max|dK| <= 1e-10 max|K|)" if s == 5 else "fixed for every step", "l2": "inputs larger than L2 (B %.1f GB)" % (B_bytes / 1e9),
                    "cluster_pairs": args.cluster_pairs,
-                   "jk_overlap": "rho and J on %d CTAs per SM beside the X split (df_build_JK)" % args.jk_overlap
+                   "jk_overlap": ("J, then K, in one stream (df_build_JK; a block-sparse B runs its masked "
+                                  "kernels in order)" if sparsity[1] < 1.0 else
+                                  "rho and J on %d CTAs per SM beside the X split (df_build_JK)" % args.jk_overlap)
                                  if args.jk_overlap else "J, then K, in one stream",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": FK / (ms_e2e * 1e-3) / 1e12 * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
